@@ -1,0 +1,169 @@
+/*
+ * sieve.h -- C ABI of the GB300 segmented prime sieve (libsieve_gb300.so).
+ *
+ * The library finds the primes of a range with the incremental segmented
+ * Sieve of Eratosthenes of "Memory Efficient Multithreaded Incremental
+ * Segmented Sieve Algorithm" (Ning & Kaeli):
+ *   - problem statement: all primes from 2 through n (Section 1.1, Figure 1);
+ *   - only candidates 6k+1 and 6k+5 are stored, one bit each, in two residue
+ *     bitmaps per segment (Section 2.1, Figure 2; the paper's A_one / A_five);
+ *   - the range is cut into contiguous segments, each owned by one worker
+ *     (Sections 2.2 and 2.3) -- here one CTA per segment, bitmaps in shared
+ *     memory;
+ *   - a base prime P starts sieving at P^2 (Section 2.4), and its first index
+ *     in each residue class of a segment comes from the Table 1 operation
+ *     (Section 3), after which the index advances by P (6P in value);
+ *   - the segments' survivors are counted or written out in increasing order
+ *     (Section 4, Figure 4: "return all k such that mod1[k] or mod5[k]").
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a sieve_status.  On failure sieve_last_error() gives a
+ *     message (thread-local, valid until the thread's next call).
+ *   - Ranges are half-open [lo, hi) unless a call says "inclusive"; n-style
+ *     calls are inclusive (primes p with 2 <= p <= n).  lo > hi is
+ *     SIEVE_ERR_INVALID; lo == hi is SIEVE_OK with nothing found.
+ *   - hi - 1 must not exceed the context's max_hi - 1 (the square of its base
+ *     table's limit covers it), else SIEVE_ERR_RANGE.  max_hi <= 2^63.
+ *   - Counts are uint64.  A checksum is the sum of the primes modulo 2^64.
+ *   - Lists are strictly increasing.
+ *   - The caller owns every buffer it passes; the library never frees or
+ *     keeps caller memory beyond the call.  The library owns everything it
+ *     allocates in a context (base table, wheel pattern, scratch) and frees it
+ *     in sieve_destroy.
+ *   - flags: SIEVE_OUT_DEVICE says that the call's output pointers are device
+ *     memory on the context's device; otherwise they are host memory.  With
+ *     SIEVE_OUT_DEVICE | SIEVE_ASYNC a count-mode call only enqueues its work
+ *     on the context's stream and returns; every other call returns after its
+ *     results are complete.
+ *   - A context is not thread-safe: one host thread at a time per context.
+ *   - Device kernels contain no unbounded waits; device-side failures are
+ *     reported through a status word read back by the host.
+ */
+#ifndef SIEVE_GB300_H
+#define SIEVE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sieve_ctx sieve_ctx;
+typedef struct sieve_server sieve_server;
+
+typedef enum {
+  SIEVE_OK = 0,
+  SIEVE_PENDING = 1,          /* server: request not finished yet            */
+  SIEVE_ERR_INVALID = -1,     /* bad argument                                  */
+  SIEVE_ERR_RANGE = -2,       /* range beyond the context's base table         */
+  SIEVE_ERR_CAPACITY = -3,    /* output buffer too small; needed size reported */
+  SIEVE_ERR_OOM = -4,         /* device or host allocation failed              */
+  SIEVE_ERR_CUDA = -5,        /* a CUDA runtime call failed                    */
+  SIEVE_ERR_TIMEOUT = -6,     /* a bounded wait ran out                        */
+  SIEVE_ERR_BUSY = -7,        /* server: admission refused (backpressure)      */
+  SIEVE_ERR_NOT_FOUND = -8    /* server: unknown or already collected request  */
+} sieve_status;
+
+typedef enum { SIEVE_COUNT = 0, SIEVE_LIST = 1 } sieve_mode;
+
+#define SIEVE_OUT_DEVICE 1u
+#define SIEVE_ASYNC 2u
+
+typedef struct {
+  uint64_t count;    /* number of primes found                 */
+  uint64_t checksum; /* sum of the primes found, modulo 2^64   */
+} sieve_count_result;
+
+/* Tunables of the segment kernels (the autotuner fills them; see
+ * sieve_autotune).  Section 5 measures how the per-thread scratch array size
+ * changes the run time; tile_bits is that knob here. */
+typedef struct {
+  uint32_t tile_bits;      /* L: candidates per residue class per segment (multiple of 1024,
+                              2 * L / 8 bytes of shared memory per CTA)                      */
+  uint32_t block_threads;  /* threads per CTA: 256, 512 or 1024                              */
+  uint32_t ctas_per_sm;    /* resident CTAs per SM the launch aims for (0: as many as fit)   */
+  uint32_t group_hits;     /* a prime is struck by a group of lanes when it has at least this
+                              many hits per lane in a segment; below that, one lane per prime */
+  uint32_t reserved[4];
+} sieve_options;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` whose calls run on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  Builds the
+ * device-resident base table of every prime <= isqrt(max_hi - 1) (the
+ * Sieve Data Store of Section 4: primes up to the square root only) and the
+ * wheel presieve pattern.  The table is built incrementally (Section 2.4):
+ * primes up to its fourth root on the host, the rest by this library's own
+ * GPU sieve.  max_hi in [2, 2^63].
+ * Errors: INVALID (max_hi out of range, ctx NULL), CUDA, OOM. */
+int sieve_create(sieve_ctx **ctx, uint64_t max_hi, int device, void *cuda_stream);
+
+/* Free everything the context owns.  NULL is ignored. */
+void sieve_destroy(sieve_ctx *ctx);
+
+/* Stream the context's calls are ordered on from now on. */
+int sieve_set_stream(sieve_ctx *ctx, void *cuda_stream);
+
+int sieve_get_options(const sieve_ctx *ctx, sieve_options *opt);
+/* Validates every field; INVALID leaves the options unchanged. */
+int sieve_set_options(sieve_ctx *ctx, const sieve_options *opt);
+
+/* Base table facts: its limit (every prime <= limit is held), the number of
+ * primes in it, and the device address of the uint32 table (owned by ctx). */
+int sieve_base_table(const sieve_ctx *ctx, uint64_t *limit, uint64_t *nprimes,
+                     const uint32_t **device_primes);
+
+/* Number of kernels this context has launched so far (every launch of the
+ * library's own kernels is counted). */
+uint64_t sieve_launch_count(const sieve_ctx *ctx);
+
+const char *sieve_last_error(void);
+
+/* ------------------------------------------------------------- range calls */
+
+/* Count of primes p with 2 <= p <= n, and their sum mod 2^64 (Section 1.1). */
+int sieve_count(sieve_ctx *ctx, uint64_t n, sieve_count_result *out);
+
+/* Primes p with 2 <= p <= n, increasing, written to out[0..cap).  *n_out gets
+ * the number of primes; if it exceeds cap the call returns CAPACITY, writes
+ * nothing past out[cap - 1] and leaves out's contents unspecified. */
+int sieve_primes(sieve_ctx *ctx, uint64_t n, uint64_t *out, size_t cap, size_t *n_out,
+                 unsigned flags);
+/* Same with uint32 output (n < 2^32, else INVALID). */
+int sieve_primes_u32(sieve_ctx *ctx, uint64_t n, uint32_t *out, size_t cap, size_t *n_out,
+                     unsigned flags);
+
+/* Primes in [lo, hi).  mode SIEVE_COUNT fills *cnt; mode SIEVE_LIST also
+ * writes the primes to out[0..cap) as uint64 with the CAPACITY rule above.
+ * cnt may be NULL in list mode.  In count mode with SIEVE_OUT_DEVICE, cnt is a
+ * device pointer to one sieve_count_result. */
+int sieve_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, int mode, sieve_count_result *cnt,
+                uint64_t *out, size_t cap, size_t *n_out, unsigned flags);
+
+/* Count, checksum and per-segment counts of the primes in [lo, hi).
+ * Segment s is the value interval [s*seg_width, (s+1)*seg_width); counts[i]
+ * holds segment floor(lo / seg_width) + i, so ncounts must equal
+ * floor((hi - 1) / seg_width) - floor(lo / seg_width) + 1 (0 when lo == hi).
+ * seg_width >= 6144.  total may be NULL.  With SIEVE_OUT_DEVICE both counts
+ * and total are device pointers. */
+int sieve_segment_counts(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t seg_width,
+                         uint64_t *counts, size_t ncounts, sieve_count_result *total,
+                         unsigned flags);
+
+/* ------------------------------------------------------------- table 1 */
+
+/* Host evaluation of the start-index routine the kernels run (Section 3,
+ * Table 1, with the P^2 start of Section 2.4).  For a segment whose index 0
+ * stands for value B (B % 6 == 0; index i of class r stands for B + 6 i + r),
+ * a start value M >= B and a prime P >= 5: *id1 / *id5 receive the smallest
+ * index i with B + 6 i + 1 (resp. + 5) a multiple of P that is >= max(M, P^2).
+ * INVALID if B % 6 != 0, M < B, P < 5 or P % 6 not in {1, 5}. */
+int sieve_table1_start(uint64_t B, uint64_t M, uint32_t P, int64_t *id1, int64_t *id5);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIEVE_GB300_H */

@@ -1,0 +1,290 @@
+"""ctypes binding of libsieve_gb300.so (include/sieve.h), argument marshalling only.
+
+Every step of the sieve runs in the library's CUDA kernels; this module only
+converts Python ints, numpy arrays (host buffers) and torch CUDA tensors
+(device buffers) into the C ABI's pointers and sizes.  There is no CPU
+fallback: if the library cannot be built or loaded, or no CUDA device is
+present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import functools
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+PENDING = 1
+ERR_INVALID = -1
+ERR_RANGE = -2
+ERR_CAPACITY = -3
+ERR_OOM = -4
+ERR_CUDA = -5
+ERR_TIMEOUT = -6
+ERR_BUSY = -7
+ERR_NOT_FOUND = -8
+
+COUNT = 0
+LIST = 1
+OUT_DEVICE = 1
+ASYNC = 2
+
+_STATUS_NAMES = {OK: "OK", PENDING: "PENDING", ERR_INVALID: "INVALID", ERR_RANGE: "RANGE",
+                 ERR_CAPACITY: "CAPACITY", ERR_OOM: "OOM", ERR_CUDA: "CUDA",
+                 ERR_TIMEOUT: "TIMEOUT", ERR_BUSY: "BUSY", ERR_NOT_FOUND: "NOT_FOUND"}
+
+
+class SieveError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        super().__init__(f"{where}: {_STATUS_NAMES.get(status, status)}: {message}")
+
+
+class CountResult(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_uint64), ("checksum", ctypes.c_uint64)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("tile_bits", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
+                ("ctas_per_sm", ctypes.c_uint32), ("group_hits", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 4)]
+
+    def as_dict(self) -> dict:
+        return {"tile_bits": self.tile_bits, "block_threads": self.block_threads,
+                "ctas_per_sm": self.ctas_per_sm, "group_hits": self.group_hits}
+
+
+_u64 = ctypes.c_uint64
+_sz = ctypes.c_size_t
+_p = ctypes.c_void_p
+_i = ctypes.c_int
+_u = ctypes.c_uint
+
+# name -> (restype, argtypes); every entry is declared in include/sieve.h
+SIGNATURES = {
+    "sieve_create": (_i, [ctypes.POINTER(_p), _u64, _i, _p]),
+    "sieve_destroy": (None, [_p]),
+    "sieve_set_stream": (_i, [_p, _p]),
+    "sieve_get_options": (_i, [_p, ctypes.POINTER(Options)]),
+    "sieve_set_options": (_i, [_p, ctypes.POINTER(Options)]),
+    "sieve_base_table": (_i, [_p, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_p)]),
+    "sieve_launch_count": (_u64, [_p]),
+    "sieve_last_error": (ctypes.c_char_p, []),
+    "sieve_count": (_i, [_p, _u64, ctypes.POINTER(CountResult)]),
+    "sieve_primes": (_i, [_p, _u64, _p, _sz, ctypes.POINTER(_sz), _u]),
+    "sieve_primes_u32": (_i, [_p, _u64, _p, _sz, ctypes.POINTER(_sz), _u]),
+    "sieve_range": (_i, [_p, _u64, _u64, _i, _p, _p, _sz, ctypes.POINTER(_sz), _u]),
+    "sieve_segment_counts": (_i, [_p, _u64, _u64, _u64, _p, _sz, _p, _u]),
+    "sieve_table1_start": (_i, [_u64, _u64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int64),
+                                ctypes.POINTER(ctypes.c_int64)]),
+}
+
+
+@functools.lru_cache(maxsize=1)
+def lib() -> ctypes.CDLL:
+    """Build (if the sources changed) and load the CUDA library."""
+    path = _build.build()
+    handle = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(handle, name)
+        fn.restype = res
+        fn.argtypes = args
+    return handle
+
+
+def last_error() -> str:
+    msg = lib().sieve_last_error()
+    return msg.decode() if msg else ""
+
+
+def _check(rc: int, where: str) -> int:
+    if rc < 0:
+        raise SieveError(rc, where, last_error())
+    return rc
+
+
+def table1_start(B: int, M: int, P: int) -> tuple[int, int]:
+    """Host evaluation of the kernels' Table 1 start-index routine."""
+    a = ctypes.c_int64(0)
+    b = ctypes.c_int64(0)
+    _check(lib().sieve_table1_start(B, M, P, ctypes.byref(a), ctypes.byref(b)), "sieve_table1_start")
+    return a.value, b.value
+
+
+def _is_torch_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+def _ptr_and_flag(x):
+    """(pointer, flags) for an output buffer: torch CUDA tensor or numpy array."""
+    if x is None:
+        return None, 0
+    if _is_torch_cuda(x):
+        if not x.is_contiguous():
+            raise ValueError("device buffers must be contiguous")
+        return x.data_ptr(), OUT_DEVICE
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("host buffers must be C-contiguous")
+        return x.ctypes.data, 0
+    raise TypeError("expected a numpy array or a torch CUDA tensor")
+
+
+def _current_stream_handle(device: int):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream(device).cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+@dataclass
+class CountAndSum:
+    count: int
+    checksum: int
+
+
+class Sieve:
+    """One library context: base table of primes <= isqrt(max_hi - 1) on `device`."""
+
+    def __init__(self, max_hi: int, device: int = 0, stream=None):
+        if stream is None:
+            stream = _current_stream_handle(device)
+        self._lib = lib()
+        h = _p()
+        _check(self._lib.sieve_create(ctypes.byref(h), int(max_hi), int(device), stream), "sieve_create")
+        self._h = h
+        self.device = device
+        self.max_hi = int(max_hi)
+
+    # lifetime -------------------------------------------------------------
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.sieve_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # configuration ----------------------------------------------------------
+    def set_stream(self, stream_handle) -> None:
+        _check(self._lib.sieve_set_stream(self._h, stream_handle), "sieve_set_stream")
+
+    def options(self) -> dict:
+        o = Options()
+        _check(self._lib.sieve_get_options(self._h, ctypes.byref(o)), "sieve_get_options")
+        return o.as_dict()
+
+    def set_options(self, **kw) -> None:
+        o = Options()
+        _check(self._lib.sieve_get_options(self._h, ctypes.byref(o)), "sieve_get_options")
+        for k, v in kw.items():
+            setattr(o, k, int(v))
+        _check(self._lib.sieve_set_options(self._h, ctypes.byref(o)), "sieve_set_options")
+
+    def base_table(self) -> tuple[int, int, int]:
+        lim = _u64(0)
+        n = _u64(0)
+        ptr = _p()
+        _check(self._lib.sieve_base_table(self._h, ctypes.byref(lim), ctypes.byref(n), ctypes.byref(ptr)),
+               "sieve_base_table")
+        return lim.value, n.value, ptr.value or 0
+
+    def launch_count(self) -> int:
+        return int(self._lib.sieve_launch_count(self._h))
+
+    # calls ------------------------------------------------------------------
+    def count(self, n: int) -> CountAndSum:
+        r = CountResult()
+        _check(self._lib.sieve_count(self._h, int(n), ctypes.byref(r)), "sieve_count")
+        return CountAndSum(r.count, r.checksum)
+
+    def primes(self, n: int, out=None, dtype=np.uint64):
+        """Primes <= n.  With `out` (numpy array or torch CUDA tensor of 4- or
+        8-byte integers) the list goes there and the count is returned;
+        without it a new numpy array is returned."""
+        if out is None:
+            c = self.count(n).count
+            out = np.empty(max(c, 1), dtype=dtype)
+            got = self.primes(n, out)
+            return out[:got]
+        ptr, flags = _ptr_and_flag(out)
+        nout = _sz(0)
+        esize = out.element_size() if _is_torch_cuda(out) else out.itemsize
+        fn = self._lib.sieve_primes_u32 if esize == 4 else self._lib.sieve_primes
+        cap = out.numel() if _is_torch_cuda(out) else out.size
+        _check(fn(self._h, int(n), ptr, cap, ctypes.byref(nout), flags), "sieve_primes")
+        return int(nout.value)
+
+    def range_count(self, lo: int, hi: int, out=None, asynchronous: bool = False):
+        """(count, checksum) of primes in [lo, hi).  With `out` = a torch CUDA
+        int64 tensor of 2 elements the result is written there (and the call
+        is only enqueued when asynchronous=True)."""
+        if out is not None:
+            ptr, flags = _ptr_and_flag(out)
+            if asynchronous:
+                flags |= ASYNC
+            _check(self._lib.sieve_range(self._h, int(lo), int(hi), COUNT, ptr, None, 0, None, flags),
+                   "sieve_range")
+            return None
+        r = CountResult()
+        _check(self._lib.sieve_range(self._h, int(lo), int(hi), COUNT, ctypes.cast(ctypes.byref(r), _p),
+                                     None, 0, None, 0), "sieve_range")
+        return CountAndSum(r.count, r.checksum)
+
+    def range_list(self, lo: int, hi: int, out=None):
+        """Primes in [lo, hi) as uint64: into `out` (returns the count) or a new array."""
+        if out is None:
+            c = self.range_count(lo, hi).count
+            out = np.empty(max(c, 1), dtype=np.uint64)
+            got = self.range_list(lo, hi, out)
+            return out[:got]
+        ptr, flags = _ptr_and_flag(out)
+        cap = out.numel() if _is_torch_cuda(out) else out.size
+        nout = _sz(0)
+        _check(self._lib.sieve_range(self._h, int(lo), int(hi), LIST, None, ptr, cap, ctypes.byref(nout), flags),
+               "sieve_range")
+        return int(nout.value)
+
+    @staticmethod
+    def nbins(lo: int, hi: int, seg_width: int) -> int:
+        return 0 if hi <= lo else (hi - 1) // seg_width - lo // seg_width + 1
+
+    def segment_counts(self, lo: int, hi: int, seg_width: int, counts=None, total=None,
+                       asynchronous: bool = False):
+        """Per-segment counts of the primes in [lo, hi).  Host mode (counts None
+        or numpy): returns (CountAndSum, counts).  Device mode (counts and total
+        torch CUDA int64 tensors): fills them and returns None."""
+        nb = self.nbins(lo, hi, seg_width)
+        if counts is not None and _is_torch_cuda(counts):
+            cptr, flags = _ptr_and_flag(counts)
+            tptr = total.data_ptr() if total is not None else None
+            if asynchronous:
+                flags |= ASYNC
+            _check(self._lib.sieve_segment_counts(self._h, int(lo), int(hi), int(seg_width), cptr, nb, tptr, flags),
+                   "sieve_segment_counts")
+            return None
+        if counts is None:
+            counts = np.zeros(max(nb, 1), dtype=np.uint64)
+        r = CountResult()
+        _check(self._lib.sieve_segment_counts(self._h, int(lo), int(hi), int(seg_width), counts.ctypes.data, nb,
+                                              ctypes.cast(ctypes.byref(r), _p), 0), "sieve_segment_counts")
+        return CountAndSum(r.count, r.checksum), counts[:nb]

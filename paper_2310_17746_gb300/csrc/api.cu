@@ -1,0 +1,485 @@
+// api.cu -- context lifetime, the device-resident base table, the wheel
+// pattern, and the public range calls of sieve.h.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "sieve_internal.cuh"
+
+namespace sieve {
+
+// ---------------------------------------------------------------- errors
+
+static thread_local char g_err[512];
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  set_error("%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? SIEVE_ERR_OOM : SIEVE_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- helpers
+
+uint64_t isqrt_u64(uint64_t n) {
+  if (n < 2) return n;
+  uint64_t x = (uint64_t)1 << ((64 - __builtin_clzll(n) + 1) / 2);
+  for (;;) {  // Newton from above
+    uint64_t y = (x + n / x) >> 1;
+    if (y >= x) break;
+    x = y;
+  }
+  while (x > n / x) x--;
+  while (x + 1 <= n / (x + 1)) x++;
+  return x;
+}
+
+uint32_t host_prime_count_le_table(const DeviceTable &t, uint64_t s) {
+  const uint32_t *b = t.host_primes, *e = t.host_primes + t.nprimes;
+  if (s >= 0xFFFFFFFFull) return t.nprimes;
+  return (uint32_t)(std::upper_bound(b, e, (uint32_t)s) - b);
+}
+
+int ensure_scratch(sieve_ctx *ctx, size_t bytes) {
+  if (bytes <= ctx->scratch_bytes) return SIEVE_OK;
+  if (ctx->d_scratch) {
+    SIEVE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->d_scratch);
+    ctx->d_scratch = nullptr;
+    ctx->scratch_bytes = 0;
+  }
+  size_t grow = bytes + bytes / 4;
+  SIEVE_CUDA_TRY(cudaMalloc(&ctx->d_scratch, grow));
+  ctx->scratch_bytes = grow;
+  return SIEVE_OK;
+}
+
+int ensure_stage(sieve_ctx *ctx, size_t bytes) {
+  if (bytes <= ctx->stage_bytes) return SIEVE_OK;
+  if (ctx->d_stage) {
+    SIEVE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->d_stage);
+    ctx->d_stage = nullptr;
+    ctx->stage_bytes = 0;
+  }
+  SIEVE_CUDA_TRY(cudaMalloc(&ctx->d_stage, bytes));
+  ctx->stage_bytes = bytes;
+  return SIEVE_OK;
+}
+
+// Wheel pattern: bit k (k mod period) of class r is 1 iff 6k + r has no
+// factor among the wheel primes.  Extended past the period so that any
+// 32-word window starting below the period can be read without wrapping.
+__global__ void wheel_pattern_kernel(uint32_t *pat) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kPatternWords) return;
+  uint32_t w1 = 0, w5 = 0;
+  for (uint32_t j = 0; j < 32; j++) {
+    uint32_t k = 32 * i + j;
+    while (k >= kWheelPeriod) k -= kWheelPeriod;
+    const uint32_t v1 = 6 * k + 1, v5 = 6 * k + 5;
+    const uint32_t wheel[6] = {5, 7, 11, 13, 17, 19};
+    bool c1 = true, c5 = true;
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+      c1 = c1 && (v1 % wheel[q] != 0);
+      c5 = c5 && (v5 % wheel[q] != 0);
+    }
+    w1 |= (uint32_t)c1 << j;
+    w5 |= (uint32_t)c5 << j;
+  }
+  pat[i] = w1;
+  pat[kPatternWords + i] = w5;
+}
+
+__global__ void reciprocal_kernel(const uint32_t *__restrict__ primes, uint64_t *__restrict__ magic, uint32_t n) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) magic[i] = reciprocal64(primes[i]);
+}
+
+// Host Eratosthenes for the first, small part of the base table.
+static std::vector<uint32_t> host_small_primes(uint32_t n) {
+  std::vector<uint8_t> a(n + 1, 1);
+  std::vector<uint32_t> out;
+  a[0] = 0;
+  if (n >= 1) a[1] = 0;
+  for (uint64_t i = 2; i * i <= n; i++)
+    if (a[i])
+      for (uint64_t j = i * i; j <= n; j += i) a[j] = 0;
+  for (uint32_t i = 2; i <= n; i++)
+    if (a[i]) out.push_back(i);
+  return out;
+}
+
+// Upper bound on pi(x) for x >= 17 (Rosser & Schoenfeld 1962: pi(x) <
+// 1.25506 x / ln x for x > 1), with slack.
+static uint64_t pi_upper(uint64_t x) {
+  if (x < 100) return 30;
+  double lx = __builtin_log((double)x);
+  return (uint64_t)(1.25506 * (double)x / lx) + 64;
+}
+
+}  // namespace sieve
+
+using namespace sieve;
+
+// ---------------------------------------------------------------- context
+
+static void free_ctx(sieve_ctx *c) {
+  if (!c) return;
+  cudaFree(c->d_primes);
+  cudaFree(c->d_magic);
+  cudaFree(c->d_pattern);
+  cudaFree(c->d_acc);
+  cudaFree(c->d_scratch);
+  cudaFree(c->d_stage);
+  if (c->h_acc) cudaFreeHost(c->h_acc);
+  delete c;
+}
+
+static sieve_options default_options() {
+  sieve_options o;
+  memset(&o, 0, sizeof(o));
+  o.tile_bits = 1u << 18;
+  o.block_threads = 512;
+  o.ctas_per_sm = 0;
+  o.group_hits = 2;
+  return o;
+}
+
+static int validate_options(const sieve_ctx *c, const sieve_options &o) {
+  if (o.tile_bits < 1024 || o.tile_bits % 1024 || o.tile_bits > (1u << 20)) {
+    set_error("tile_bits must be a multiple of 1024 in [1024, 2^20]");
+    return SIEVE_ERR_INVALID;
+  }
+  if ((int)(o.tile_bits / 4) > c->smem_optin) {
+    set_error("tile_bits %u needs %u bytes of shared memory; the device allows %d", o.tile_bits,
+              o.tile_bits / 4, c->smem_optin);
+    return SIEVE_ERR_INVALID;
+  }
+  if (o.block_threads != 256 && o.block_threads != 512 && o.block_threads != 1024) {
+    set_error("block_threads must be 256, 512 or 1024");
+    return SIEVE_ERR_INVALID;
+  }
+  if (o.ctas_per_sm > 32) {
+    set_error("ctas_per_sm must be <= 32");
+    return SIEVE_ERR_INVALID;
+  }
+  if (o.group_hits == 0 || o.group_hits > 1024) {
+    set_error("group_hits must be in [1, 1024]");
+    return SIEVE_ERR_INVALID;
+  }
+  return SIEVE_OK;
+}
+
+static int build_base_table(sieve_ctx *c, uint64_t limit) {
+  // Section 2.4 / Section 4: the sieving primes are only those up to the
+  // square root; they are themselves found incrementally.  Primes <= sqrt(limit)
+  // come from a host sieve, the rest from this library's GPU sieve using them.
+  const uint32_t small_n = (uint32_t)isqrt_u64(limit) + 1;
+  std::vector<uint32_t> small = host_small_primes(small_n);
+  const uint64_t cap = pi_upper(limit);
+  SIEVE_CUDA_TRY(cudaMalloc(&c->d_primes, cap * sizeof(uint32_t)));
+  SIEVE_CUDA_TRY(cudaMalloc(&c->d_magic, cap * sizeof(uint64_t)));
+  SIEVE_CUDA_TRY(cudaMemcpyAsync(c->d_primes, small.data(), small.size() * sizeof(uint32_t),
+                                 cudaMemcpyHostToDevice, c->stream));
+  const uint32_t ns = (uint32_t)small.size();
+  reciprocal_kernel<<<(ns + 255) / 256, 256, 0, c->stream>>>(c->d_primes, c->d_magic, ns);
+  c->launches++;
+  SIEVE_CUDA_TRY(cudaGetLastError());
+
+  DeviceTable t0;
+  t0.primes = c->d_primes;
+  t0.magic = c->d_magic;
+  t0.host_primes = small.data();
+  t0.nprimes = ns;
+  t0.limit = small_n;
+  uint64_t total = ns;
+  if (limit > small_n) {
+    RangeRequest rq;
+    rq.lo = (uint64_t)small_n + 1;
+    rq.hi = limit + 1;
+    rq.list = 1;
+    rq.out_bytes = 4;
+    rq.out = c->d_primes + ns;
+    rq.cap = cap - ns;
+    rq.out_on_device = 1;
+    size_t n = 0;
+    int rc = run_range(c, t0, rq, &n);
+    if (rc != SIEVE_OK) return rc;
+    total += n;
+    if (n) {
+      reciprocal_kernel<<<(uint32_t)((n + 255) / 256), 256, 0, c->stream>>>(c->d_primes + ns, c->d_magic + ns,
+                                                                           (uint32_t)n);
+      c->launches++;
+      SIEVE_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  c->h_primes.resize(total);
+  SIEVE_CUDA_TRY(cudaMemcpyAsync(c->h_primes.data(), c->d_primes, total * sizeof(uint32_t),
+                                 cudaMemcpyDeviceToHost, c->stream));
+  SIEVE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->table.primes = c->d_primes;
+  c->table.magic = c->d_magic;
+  c->table.host_primes = c->h_primes.data();
+  c->table.nprimes = (uint32_t)total;
+  c->table.limit = limit;
+  return SIEVE_OK;
+}
+
+extern "C" int sieve_create(sieve_ctx **ctx, uint64_t max_hi, int device, void *cuda_stream) {
+  if (!ctx) {
+    set_error("ctx is NULL");
+    return SIEVE_ERR_INVALID;
+  }
+  *ctx = nullptr;
+  if (max_hi < 2 || max_hi > (1ull << 63)) {
+    set_error("max_hi must be in [2, 2^63]");
+    return SIEVE_ERR_INVALID;
+  }
+  sieve_ctx *c = new (std::nothrow) sieve_ctx();
+  if (!c) {
+    set_error("host allocation failed");
+    return SIEVE_ERR_OOM;
+  }
+  int rc = SIEVE_OK;
+  do {
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "cudaSetDevice");
+      break;
+    }
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->max_hi = max_hi;
+    if ((e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device)) !=
+            cudaSuccess) {
+      rc = cuda_fail(e, "cudaDeviceGetAttribute");
+      break;
+    }
+    // keep room for the kernels' static shared memory
+    c->smem_optin -= 2048;
+    if ((rc = range_set_smem_attributes(c->smem_optin)) != SIEVE_OK) break;
+    c->opt = default_options();
+    while (c->opt.tile_bits / 4 > (uint32_t)c->smem_optin) c->opt.tile_bits /= 2;
+    c->acc_words = 16;
+    if ((e = cudaMalloc(&c->d_acc, c->acc_words * sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMallocHost(&c->h_acc, c->acc_words * sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_pattern, 2 * kPatternWords * sizeof(uint32_t))) != cudaSuccess) {
+      rc = cuda_fail(e, "context allocation");
+      break;
+    }
+    wheel_pattern_kernel<<<(kPatternWords + 255) / 256, 256, 0, c->stream>>>(c->d_pattern);
+    c->launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+      rc = cuda_fail(e, "wheel_pattern_kernel");
+      break;
+    }
+    const uint64_t limit = std::max<uint64_t>(isqrt_u64(max_hi - 1), 1u << 16);
+    rc = build_base_table(c, limit);
+  } while (0);
+  if (rc != SIEVE_OK) {
+    free_ctx(c);
+    return rc;
+  }
+  *ctx = c;
+  return SIEVE_OK;
+}
+
+extern "C" void sieve_destroy(sieve_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  free_ctx(ctx);
+}
+
+extern "C" int sieve_set_stream(sieve_ctx *ctx, void *cuda_stream) {
+  if (!ctx) {
+    set_error("ctx is NULL");
+    return SIEVE_ERR_INVALID;
+  }
+  ctx->stream = (cudaStream_t)cuda_stream;
+  return SIEVE_OK;
+}
+
+extern "C" int sieve_get_options(const sieve_ctx *ctx, sieve_options *opt) {
+  if (!ctx || !opt) {
+    set_error("NULL argument");
+    return SIEVE_ERR_INVALID;
+  }
+  *opt = ctx->opt;
+  return SIEVE_OK;
+}
+
+extern "C" int sieve_set_options(sieve_ctx *ctx, const sieve_options *opt) {
+  if (!ctx || !opt) {
+    set_error("NULL argument");
+    return SIEVE_ERR_INVALID;
+  }
+  int rc = validate_options(ctx, *opt);
+  if (rc != SIEVE_OK) return rc;
+  ctx->opt = *opt;
+  return SIEVE_OK;
+}
+
+extern "C" int sieve_base_table(const sieve_ctx *ctx, uint64_t *limit, uint64_t *nprimes,
+                                const uint32_t **device_primes) {
+  if (!ctx) {
+    set_error("ctx is NULL");
+    return SIEVE_ERR_INVALID;
+  }
+  if (limit) *limit = ctx->table.limit;
+  if (nprimes) *nprimes = ctx->table.nprimes;
+  if (device_primes) *device_primes = ctx->table.primes;
+  return SIEVE_OK;
+}
+
+extern "C" uint64_t sieve_launch_count(const sieve_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" const char *sieve_last_error(void) { return g_err; }
+
+// ---------------------------------------------------------------- range calls
+
+static int enter(sieve_ctx *ctx) {
+  if (!ctx) {
+    set_error("ctx is NULL");
+    return SIEVE_ERR_INVALID;
+  }
+  g_err[0] = 0;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  return SIEVE_OK;
+}
+
+extern "C" int sieve_count(sieve_ctx *ctx, uint64_t n, sieve_count_result *out) {
+  int rc = enter(ctx);
+  if (rc != SIEVE_OK) return rc;
+  if (!out) {
+    set_error("out is NULL");
+    return SIEVE_ERR_INVALID;
+  }
+  if (n >= (1ull << 63)) {
+    set_error("n must be < 2^63");
+    return SIEVE_ERR_RANGE;
+  }
+  RangeRequest rq;
+  rq.lo = 0;
+  rq.hi = n + 1;
+  rq.total = out;
+  return run_range(ctx, ctx->table, rq, nullptr);
+}
+
+static int primes_common(sieve_ctx *ctx, uint64_t n, void *out, size_t cap, size_t *n_out, unsigned flags,
+                         int bytes) {
+  int rc = enter(ctx);
+  if (rc != SIEVE_OK) return rc;
+  if (!n_out || (!out && cap)) {
+    set_error("NULL argument");
+    return SIEVE_ERR_INVALID;
+  }
+  if (bytes == 4 && n > 0xFFFFFFFFull) {
+    set_error("uint32 output needs n < 2^32");
+    return SIEVE_ERR_INVALID;
+  }
+  if (n >= (1ull << 63)) {
+    set_error("n must be < 2^63");
+    return SIEVE_ERR_RANGE;
+  }
+  RangeRequest rq;
+  rq.lo = 0;
+  rq.hi = n + 1;
+  rq.list = 1;
+  rq.out_bytes = bytes;
+  rq.out = out;
+  rq.cap = cap;
+  rq.out_on_device = (flags & SIEVE_OUT_DEVICE) != 0;
+  return run_range(ctx, ctx->table, rq, n_out);
+}
+
+extern "C" int sieve_primes(sieve_ctx *ctx, uint64_t n, uint64_t *out, size_t cap, size_t *n_out,
+                            unsigned flags) {
+  return primes_common(ctx, n, out, cap, n_out, flags, 8);
+}
+
+extern "C" int sieve_primes_u32(sieve_ctx *ctx, uint64_t n, uint32_t *out, size_t cap, size_t *n_out,
+                                unsigned flags) {
+  return primes_common(ctx, n, out, cap, n_out, flags, 4);
+}
+
+extern "C" int sieve_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, int mode, sieve_count_result *cnt,
+                           uint64_t *out, size_t cap, size_t *n_out, unsigned flags) {
+  int rc = enter(ctx);
+  if (rc != SIEVE_OK) return rc;
+  if (mode != SIEVE_COUNT && mode != SIEVE_LIST) {
+    set_error("mode must be SIEVE_COUNT or SIEVE_LIST");
+    return SIEVE_ERR_INVALID;
+  }
+  if (mode == SIEVE_COUNT && !cnt) {
+    set_error("cnt is NULL in count mode");
+    return SIEVE_ERR_INVALID;
+  }
+  if (mode == SIEVE_LIST && (!n_out || (!out && cap))) {
+    set_error("list mode needs n_out and an output buffer");
+    return SIEVE_ERR_INVALID;
+  }
+  RangeRequest rq;
+  rq.lo = lo;
+  rq.hi = hi;
+  rq.list = mode == SIEVE_LIST;
+  rq.out_bytes = 8;
+  rq.out = out;
+  rq.cap = cap;
+  rq.out_on_device = (flags & SIEVE_OUT_DEVICE) != 0;
+  rq.total = cnt;
+  rq.async = mode == SIEVE_COUNT && (flags & SIEVE_OUT_DEVICE) && (flags & SIEVE_ASYNC);
+  return run_range(ctx, ctx->table, rq, n_out);
+}
+
+extern "C" int sieve_segment_counts(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t seg_width,
+                                    uint64_t *counts, size_t ncounts, sieve_count_result *total,
+                                    unsigned flags) {
+  int rc = enter(ctx);
+  if (rc != SIEVE_OK) return rc;
+  if (seg_width == 0 || (!counts && ncounts)) {
+    set_error("seg_width must be > 0 and counts non-NULL");
+    return SIEVE_ERR_INVALID;
+  }
+  RangeRequest rq;
+  rq.lo = lo;
+  rq.hi = hi;
+  rq.seg_width = seg_width;
+  rq.bins = counts;
+  rq.nbins = ncounts;
+  rq.total = total;
+  rq.out_on_device = (flags & SIEVE_OUT_DEVICE) != 0;
+  rq.async = (flags & SIEVE_OUT_DEVICE) && (flags & SIEVE_ASYNC);
+  return run_range(ctx, ctx->table, rq, nullptr);
+}
+
+// ---------------------------------------------------------------- table 1 (host)
+
+extern "C" int sieve_table1_start(uint64_t B, uint64_t M, uint32_t P, int64_t *id1, int64_t *id5) {
+  if (!id1 || !id5 || B % 6 != 0 || M < B || P < 5 || (P % 6 != 1 && P % 6 != 5) ||
+      M >= (1ull << 63) || B >= (1ull << 63)) {
+    set_error("sieve_table1_start: invalid argument");
+    return SIEVE_ERR_INVALID;
+  }
+  const uint64_t P2 = (uint64_t)P * P;
+  const uint64_t Mp = M > P2 ? M : P2;
+  if (Mp - B >= (1ull << 62)) {
+    set_error("sieve_table1_start: max(M, P^2) - B too large");
+    return SIEVE_ERR_INVALID;
+  }
+  StartIndex s = table1_start(B, M, P, reciprocal64(P));
+  *id1 = s.id1;
+  *id5 = s.id5;
+  return SIEVE_OK;
+}

@@ -1,0 +1,549 @@
+// range.cu -- sieve of one range [lo, hi): count / checksum / per-segment
+// counts, or the full increasing list.
+//
+// Kernel structure (Section 4, Figure 4, mapped to a GPU): the range is cut
+// into tiles of L indices per residue class; CTAs take tiles in grid-stride
+// order.  Per tile: wheel presieve copy -> Table 1 start indices and strikes
+// for every base prime 23 <= P <= isqrt(tile end) -> fix-ups -> popcount,
+// checksum and per-segment counts (count mode) or bitmap write-out (list mode,
+// followed by a scan of per-tile counts and a compaction kernel).
+#include <algorithm>
+#include <cstring>
+
+#include "tile.cuh"
+
+namespace sieve {
+
+struct RangeKernelParams {
+  uint64_t lo, hi;          // [lo, hi)
+  uint64_t k_begin;         // class index of tile 0's index 0
+  uint64_t k_end;           // ceil((hi - 1) / 6): indices below it can hold a value < hi
+  uint32_t L;               // indices per class per tile (multiple of 32)
+  uint32_t ntiles;
+  const uint32_t *primes;
+  const uint64_t *magic;
+  uint32_t nprimes;         // primes[0..nprimes) cover isqrt(hi - 1)
+  uint32_t i_split;         // primes with index < i_split are struck by a warp
+  const uint32_t *pattern;  // wheel pattern, class 1 then class 5
+  // count-mode outputs (atomically accumulated)
+  unsigned long long *count;
+  unsigned long long *checksum;
+  uint64_t seg_width;       // 0: no per-segment counts
+  uint64_t first_seg;       // floor(lo / seg_width)
+  unsigned long long *bins;
+  // list mode
+  uint32_t *tile_counts;    // per tile
+  uint2 *bitmap;            // per tile L/32 (class-1 word, class-5 word) pairs
+};
+
+template <int BLOCK, bool LIST>
+__global__ void __launch_bounds__(BLOCK) range_tiles_kernel(const RangeKernelParams p) {
+  constexpr int NWARPS = BLOCK / 32;
+  extern __shared__ uint32_t smem[];
+  uint32_t *s1 = smem;
+  uint32_t *s5 = smem + p.L / 32;
+  __shared__ uint32_t sh_np;
+  __shared__ uint64_t sh_bin0;
+  __shared__ int64_t sh_t1, sh_t5;
+  __shared__ int sh_has_boundary;
+  __shared__ uint64_t red[3 * NWARPS];
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  for (uint32_t t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
+    const uint64_t K0 = p.k_begin + (uint64_t)t * p.L;
+    const uint64_t left = p.k_end - K0;
+    const uint32_t len = left < p.L ? (uint32_t)left : p.L;
+    const uint32_t nwords = (len + 31) / 32;
+    const uint64_t B = 6 * K0;
+    const uint64_t tile_end = B + 6ull * len;
+    const uint64_t vend = tile_end < p.hi ? tile_end : p.hi;
+
+    if (warp == 0) {
+      // base primes needed: P <= isqrt(vend - 1)
+      const uint64_t s = vend >= 2 ? isqrt_dev(vend - 1) : 0;
+      const uint32_t np = warp_count_le(p.primes, p.nprimes, s);
+      if (lane == 0) {
+        sh_np = np;
+        sh_has_boundary = 0;
+        if (p.seg_width) {
+          const uint64_t v0 = B > p.lo ? B : p.lo;
+          const uint64_t sg = v0 / p.seg_width;
+          sh_bin0 = sg - p.first_seg;
+          const uint64_t X = (sg + 1) * p.seg_width;
+          if (X < vend) {
+            sh_has_boundary = 1;
+            int64_t t1 = ceil_div6((int64_t)(X - B) - 1), t5 = ceil_div6((int64_t)(X - B) - 5);
+            sh_t1 = t1 < 0 ? 0 : (t1 > (int64_t)len ? (int64_t)len : t1);
+            sh_t5 = t5 < 0 ? 0 : (t5 > (int64_t)len ? (int64_t)len : t5);
+          }
+        }
+      }
+    }
+    presieve_copy<NWARPS>(s1, s5, nwords, K0, p.pattern);
+    __syncthreads();
+
+    strike_primes<BLOCK>(s1, s5, B, len, p.primes, p.magic, kFirstSievingPrimeIndex, p.i_split, sh_np);
+    __syncthreads();
+
+    const ValidRange v = valid_range(p.lo, p.hi, B, len);
+    fixup_tile<BLOCK>(s1, s5, nwords, K0, v);
+    __syncthreads();
+
+    // popcount, checksum, and the count below the segment boundary (if any)
+    uint64_t cnt = 0, sum = 0, below = 0;
+    const int has_b = sh_has_boundary;
+    const int64_t t1 = has_b ? sh_t1 : 0, t5 = has_b ? sh_t5 : 0;
+    for (uint32_t w = threadIdx.x; w < nwords; w += BLOCK) {
+      const uint32_t a = s1[w], b = s5[w];
+      if (LIST) p.bitmap[(uint64_t)t * (p.L / 32) + w] = make_uint2(a, b);
+      const uint32_t ca = __popc(a), cb = __popc(b);
+      cnt += ca + cb;
+      const uint64_t vb = 6 * (K0 + 32ull * w);
+      sum += (uint64_t)ca * (vb + 1) + (uint64_t)cb * (vb + 5) +
+             6ull * (uint64_t)(bit_index_sum(a) + bit_index_sum(b));
+      if (has_b) {
+        const int64_t base = 32 * (int64_t)w;
+        below += __popc(a & bit_range_mask(0, t1 - base)) + __popc(b & bit_range_mask(0, t5 - base));
+      }
+    }
+    block_sum3<BLOCK>(cnt, sum, below, red);
+    if (threadIdx.x == 0) {
+      if (K0 == 0) {  // 2 and 3 are outside the residue arrays (Section 2.1)
+        const uint64_t e2 = (p.lo <= 2 && 2 < p.hi), e3 = (p.lo <= 3 && 3 < p.hi);
+        cnt += e2 + e3;
+        below += e2 + e3;
+        sum += 2 * e2 + 3 * e3;
+      }
+      if (LIST) {
+        p.tile_counts[t] = (uint32_t)cnt;
+      }
+      if (p.count) atomicAdd(p.count, (unsigned long long)cnt);
+      if (p.checksum) atomicAdd(p.checksum, (unsigned long long)sum);
+      if (p.seg_width && cnt) {
+        if (has_b) {
+          if (below) atomicAdd(p.bins + sh_bin0, (unsigned long long)below);
+          if (cnt - below) atomicAdd(p.bins + sh_bin0 + 1, (unsigned long long)(cnt - below));
+        } else {
+          atomicAdd(p.bins + sh_bin0, (unsigned long long)cnt);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Exclusive scan of per-tile counts into 64-bit offsets; total at offsets[n].
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) scan_tile_counts_kernel(const uint32_t *__restrict__ counts,
+                                                                 uint64_t *__restrict__ offsets,
+                                                                 uint32_t n) {
+  constexpr int NWARPS = BLOCK / 32;
+  __shared__ uint64_t warp_tot[NWARPS];
+  __shared__ uint64_t carry;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < n; base += BLOCK) {
+    const uint32_t i = base + threadIdx.x;
+    const uint64_t x = i < n ? counts[i] : 0;
+    uint64_t incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint64_t y = __shfl_up_sync(kFullMask, incl, o);
+      if (lane >= (uint32_t)o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      uint64_t wt = lane < NWARPS ? warp_tot[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint64_t y = __shfl_up_sync(kFullMask, wt, o);
+        if (lane >= (uint32_t)o) wt += y;
+      }
+      if (lane < NWARPS) warp_tot[lane] = wt;  // inclusive over warps
+    }
+    __syncthreads();
+    const uint64_t before = carry + (warp > 0 ? warp_tot[warp - 1] : 0);
+    if (i < n) offsets[i] = before + incl - x;
+    __syncthreads();
+    if (threadIdx.x == BLOCK - 1) carry = before + incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) offsets[n] = carry;
+}
+
+struct CompactParams {
+  uint64_t lo, hi, k_begin, k_end;
+  uint32_t L, ntiles;
+  const uint2 *bitmap;
+  const uint64_t *offsets;  // ntiles + 1 entries; offsets[ntiles] = total
+  void *out;
+  uint64_t cap;
+};
+
+// List compaction: per tile, each warp owns a contiguous run of words; a
+// first pass counts the warp's primes, a block scan places the warps, a
+// second pass interleaves class-1 / class-5 bits in value order, scans the
+// lanes' counts with shuffles and writes the values.
+template <int BLOCK, typename OutT>
+__global__ void __launch_bounds__(BLOCK) compact_kernel(const CompactParams p) {
+  constexpr int NWARPS = BLOCK / 32;
+  __shared__ uint64_t warp_base[NWARPS];
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (p.offsets[p.ntiles] > p.cap) return;  // capacity: the host reports it
+  OutT *out = (OutT *)p.out;
+  for (uint32_t t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
+    const uint64_t K0 = p.k_begin + (uint64_t)t * p.L;
+    const uint64_t left = p.k_end - K0;
+    const uint32_t len = left < p.L ? (uint32_t)left : p.L;
+    const uint32_t nwords = (len + 31) / 32;
+    const uint2 *bm = p.bitmap + (uint64_t)t * (p.L / 32);
+    uint64_t off = p.offsets[t];
+    if (K0 == 0) {  // 2 and 3 first
+      if (threadIdx.x == 0) {
+        uint64_t o = off;
+        if (p.lo <= 2 && 2 < p.hi) out[o++] = (OutT)2;
+        if (p.lo <= 3 && 3 < p.hi) out[o++] = (OutT)3;
+      }
+      off += (p.lo <= 2 && 2 < p.hi) + (p.lo <= 3 && 3 < p.hi);
+    }
+    uint32_t per_warp = (nwords + NWARPS - 1) / NWARPS;
+    per_warp = (per_warp + 31) & ~31u;
+    const uint32_t w_begin = warp * per_warp;
+    const uint32_t w_end = min(w_begin + per_warp, nwords);
+    uint32_t c = 0;
+    for (uint32_t w = w_begin + lane; w < w_end; w += 32) {
+      const uint2 x = bm[w];
+      c += __popc(x.x) + __popc(x.y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFullMask, c, o);
+    if (lane == 0) warp_base[warp] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint64_t run = off;
+      for (int i = 0; i < NWARPS; i++) {
+        const uint64_t ci = warp_base[i];
+        warp_base[i] = run;
+        run += ci;
+      }
+    }
+    __syncthreads();
+    uint64_t base = warp_base[warp];
+    for (uint32_t w0 = w_begin; w0 < w_end; w0 += 32) {
+      const uint32_t w = w0 + lane;
+      uint64_t z = 0;
+      if (w < w_end) {
+        const uint2 x = bm[w];
+        z = interleave_classes(x.x, x.y);
+      }
+      const uint32_t n = __popcll(z);
+      uint32_t incl = n;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(kFullMask, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
+      }
+      uint64_t pos = base + incl - n;
+      const uint64_t vb = 6 * (K0 + 32ull * w);
+      while (z) {
+        const uint32_t j = __ffsll((long long)z) - 1;
+        z &= z - 1;
+        out[pos++] = (OutT)(vb + 6ull * (j >> 1) + ((j & 1) ? 5u : 1u));
+      }
+      base += __shfl_sync(kFullMask, incl, 31);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+namespace {
+
+template <int BLOCK>
+int launch_range_tiles(sieve_ctx *ctx, const RangeKernelParams &p, bool list, int grid, size_t smem) {
+  if (list)
+    range_tiles_kernel<BLOCK, true><<<grid, BLOCK, smem, ctx->stream>>>(p);
+  else
+    range_tiles_kernel<BLOCK, false><<<grid, BLOCK, smem, ctx->stream>>>(p);
+  ctx->launches++;
+  SIEVE_CUDA_TRY(cudaGetLastError());
+  return SIEVE_OK;
+}
+
+template <int BLOCK>
+int occupancy(int *blocks, bool list, size_t smem) {
+  cudaError_t e = list ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, range_tiles_kernel<BLOCK, true>,
+                                                                       BLOCK, smem)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, range_tiles_kernel<BLOCK, false>,
+                                                                       BLOCK, smem);
+  SIEVE_CUDA_TRY(e);
+  return SIEVE_OK;
+}
+
+template <int BLOCK>
+int set_smem_attr(int bytes) {
+  SIEVE_CUDA_TRY(cudaFuncSetAttribute(range_tiles_kernel<BLOCK, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  SIEVE_CUDA_TRY(cudaFuncSetAttribute(range_tiles_kernel<BLOCK, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  return SIEVE_OK;
+}
+
+int dispatch_occupancy(int threads, int *blocks, bool list, size_t smem) {
+  switch (threads) {
+    case 256: return occupancy<256>(blocks, list, smem);
+    case 512: return occupancy<512>(blocks, list, smem);
+    default: return occupancy<1024>(blocks, list, smem);
+  }
+}
+
+int dispatch_launch(sieve_ctx *ctx, int threads, const RangeKernelParams &p, bool list, int grid, size_t smem) {
+  switch (threads) {
+    case 256: return launch_range_tiles<256>(ctx, p, list, grid, smem);
+    case 512: return launch_range_tiles<512>(ctx, p, list, grid, smem);
+    default: return launch_range_tiles<1024>(ctx, p, list, grid, smem);
+  }
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+int range_set_smem_attributes(int bytes) {
+  int rc;
+  if ((rc = set_smem_attr<256>(bytes)) != SIEVE_OK) return rc;
+  if ((rc = set_smem_attr<512>(bytes)) != SIEVE_OK) return rc;
+  return set_smem_attr<1024>(bytes);
+}
+
+// Largest multiple of 32 that is <= x.
+static uint32_t floor32(uint64_t x) { return (uint32_t)(x & ~31ull); }
+
+int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req, size_t *n_out) {
+  if (n_out) *n_out = 0;
+  if (req.lo > req.hi) {
+    set_error("lo (%llu) > hi (%llu)", (unsigned long long)req.lo, (unsigned long long)req.hi);
+    return SIEVE_ERR_INVALID;
+  }
+  if (req.hi > (1ull << 63)) {
+    set_error("hi must be <= 2^63");
+    return SIEVE_ERR_RANGE;
+  }
+  if (req.seg_width) {
+    if (req.seg_width < 6144) {
+      set_error("seg_width must be >= 6144");
+      return SIEVE_ERR_INVALID;
+    }
+    const size_t need = req.hi > req.lo ? (size_t)((req.hi - 1) / req.seg_width - req.lo / req.seg_width + 1) : 0;
+    if (req.nbins != need) {
+      set_error("ncounts must be %zu for this range and seg_width", need);
+      return SIEVE_ERR_INVALID;
+    }
+  }
+  const bool dev_out = req.out_on_device != 0;
+  cudaStream_t st = ctx->stream;
+
+  // empty range: zero every output
+  if (req.lo == req.hi) {
+    if (req.total) {
+      if (dev_out) {
+        SIEVE_CUDA_TRY(cudaMemsetAsync(req.total, 0, sizeof(sieve_count_result), st));
+      } else {
+        req.total->count = 0;
+        req.total->checksum = 0;
+      }
+    }
+    if (!req.async) SIEVE_CUDA_TRY(cudaStreamSynchronize(st));
+    return SIEVE_OK;
+  }
+  const uint64_t s = isqrt_u64(req.hi - 1);
+  if (s > table.limit) {
+    set_error("isqrt(hi - 1) = %llu exceeds the base table limit %llu (context max_hi too small)",
+              (unsigned long long)s, (unsigned long long)table.limit);
+    return SIEVE_ERR_RANGE;
+  }
+
+  // tiles
+  const uint64_t k_begin = req.lo / 6;
+  const uint64_t k_end = (req.hi + 4) / 6;  // ceil((hi - 1) / 6)
+  const uint64_t span = k_end > k_begin ? k_end - k_begin : 0;
+  const int threads = (int)ctx->opt.block_threads;
+  uint32_t L = ctx->opt.tile_bits;
+  if (req.seg_width) {  // at most one segment boundary per tile: 6 L <= seg_width
+    const uint32_t lw = floor32(req.seg_width / 6);
+    if (lw < L) L = lw;
+  }
+  size_t smem = (size_t)L / 4;
+  int per_sm = 0;
+  int rc = dispatch_occupancy(threads, &per_sm, req.list != 0, smem);
+  if (rc != SIEVE_OK) return rc;
+  if (per_sm < 1) {
+    set_error("tile of %u bits does not fit on an SM", L);
+    return SIEVE_ERR_INVALID;
+  }
+  if (ctx->opt.ctas_per_sm && (int)ctx->opt.ctas_per_sm < per_sm) per_sm = (int)ctx->opt.ctas_per_sm;
+  const uint64_t slots = (uint64_t)ctx->num_sms * (uint64_t)per_sm;
+  // small ranges: shrink tiles so that every CTA slot gets work
+  if (span > 0 && span < (uint64_t)L * slots) {
+    uint64_t want = (span + slots - 1) / slots;
+    want = (want + 1023) / 1024 * 1024;
+    if (want < L) L = (uint32_t)want;
+    smem = (size_t)L / 4;
+  }
+  const uint64_t ntiles64 = span ? (span + L - 1) / L : 0;
+  if (ntiles64 > 0xFFFFFFF0ull) {
+    set_error("range needs too many tiles");
+    return SIEVE_ERR_INVALID;
+  }
+  const uint32_t ntiles = (uint32_t)ntiles64;
+  const int grid = (int)std::min<uint64_t>(ntiles ? ntiles : 1, slots);
+
+  // primes needed and the warp/lane split: a warp takes a prime while it has
+  // >= group_hits hits per lane in a tile, i.e. P <= L / (32 * group_hits)
+  const uint32_t np = host_prime_count_le_table(table, s);
+  const uint64_t gmax = L / (32ull * std::max<uint32_t>(1u, ctx->opt.group_hits));
+  const uint32_t i_split = host_prime_count_le_table(table, gmax);
+
+  RangeKernelParams p;
+  memset(&p, 0, sizeof(p));
+  p.lo = req.lo;
+  p.hi = req.hi;
+  p.k_begin = k_begin;
+  p.k_end = k_end;
+  p.L = L;
+  p.ntiles = ntiles;
+  p.primes = table.primes;
+  p.magic = table.magic;
+  p.nprimes = np;
+  p.i_split = i_split;
+  p.pattern = ctx->d_pattern;
+  p.seg_width = req.seg_width;
+  p.first_seg = req.seg_width ? req.lo / req.seg_width : 0;
+
+  // where count / checksum / bins accumulate
+  unsigned long long *acc = ctx->d_acc;  // [0] count, [1] checksum
+  const bool total_direct = dev_out && req.total && !req.list;
+  if (total_direct) {
+    p.count = (unsigned long long *)&req.total->count;
+    p.checksum = (unsigned long long *)&req.total->checksum;
+    SIEVE_CUDA_TRY(cudaMemsetAsync(req.total, 0, sizeof(sieve_count_result), st));
+  } else {
+    p.count = acc;
+    p.checksum = acc + 1;
+    SIEVE_CUDA_TRY(cudaMemsetAsync(acc, 0, 2 * sizeof(unsigned long long), st));
+  }
+
+  // scratch layout: [bins (host-output case)] [tile counts] [offsets] [bitmap] [list staging]
+  size_t off_bins = 0, off_counts = 0, off_offsets = 0, off_bitmap = 0, need = 0;
+  const bool bins_direct = dev_out;
+  if (req.seg_width && !bins_direct) {
+    off_bins = need;
+    need = align_up(need + req.nbins * sizeof(uint64_t), 256);
+  }
+  if (req.list) {
+    off_counts = need;
+    need = align_up(need + (size_t)ntiles * sizeof(uint32_t), 256);
+    off_offsets = need;
+    need = align_up(need + ((size_t)ntiles + 1) * sizeof(uint64_t), 256);
+    off_bitmap = need;
+    need = align_up(need + (size_t)ntiles * (L / 32) * sizeof(uint2), 256);
+  }
+  if (need) {
+    rc = ensure_scratch(ctx, need);
+    if (rc != SIEVE_OK) return rc;
+  }
+  char *scr = (char *)ctx->d_scratch;
+  if (req.seg_width) {
+    p.bins = bins_direct ? (unsigned long long *)req.bins : (unsigned long long *)(scr + off_bins);
+    SIEVE_CUDA_TRY(cudaMemsetAsync(p.bins, 0, req.nbins * sizeof(uint64_t), st));
+  }
+  if (req.list) {
+    p.tile_counts = (uint32_t *)(scr + off_counts);
+    p.bitmap = (uint2 *)(scr + off_bitmap);
+  }
+
+  if (ntiles) {
+    rc = dispatch_launch(ctx, threads, p, req.list != 0, grid, smem);
+    if (rc != SIEVE_OK) return rc;
+  }
+
+  if (!req.list) {
+    if (!dev_out) {
+      SIEVE_CUDA_TRY(cudaMemcpyAsync(ctx->h_acc, acc, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+      if (req.seg_width)
+        SIEVE_CUDA_TRY(cudaMemcpyAsync(req.bins, p.bins, req.nbins * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+      SIEVE_CUDA_TRY(cudaStreamSynchronize(st));
+      if (req.total) {
+        req.total->count = ctx->h_acc[0];
+        req.total->checksum = ctx->h_acc[1];
+      }
+    } else if (!req.async) {
+      SIEVE_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return SIEVE_OK;
+  }
+
+  // list mode: scan, read the total, compact
+  uint64_t *offsets = (uint64_t *)(scr + off_offsets);
+  if (ntiles) {
+    scan_tile_counts_kernel<1024><<<1, 1024, 0, st>>>(p.tile_counts, offsets, ntiles);
+    ctx->launches++;
+    SIEVE_CUDA_TRY(cudaGetLastError());
+    SIEVE_CUDA_TRY(cudaMemcpyAsync(ctx->h_acc + 2, offsets + ntiles, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+  } else {
+    ctx->h_acc[2] = 0;
+  }
+  SIEVE_CUDA_TRY(cudaMemcpyAsync(ctx->h_acc, acc, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  SIEVE_CUDA_TRY(cudaStreamSynchronize(st));
+  const uint64_t total = ctx->h_acc[2];
+  if (n_out) *n_out = (size_t)total;
+  if (req.total) {
+    sieve_count_result r{ctx->h_acc[0], ctx->h_acc[1]};
+    if (dev_out)
+      SIEVE_CUDA_TRY(cudaMemcpyAsync(req.total, &r, sizeof(r), cudaMemcpyHostToDevice, st));
+    else
+      *req.total = r;
+  }
+  if (total > req.cap) {
+    set_error("output capacity %zu is below the %llu primes found", req.cap, (unsigned long long)total);
+    if (dev_out) SIEVE_CUDA_TRY(cudaStreamSynchronize(st));
+    return SIEVE_ERR_CAPACITY;
+  }
+  if (total == 0) {
+    if (dev_out) SIEVE_CUDA_TRY(cudaStreamSynchronize(st));
+    return SIEVE_OK;
+  }
+  void *dst = req.out;
+  if (!dev_out) {  // stage on the device, then copy to the caller's host buffer
+    rc = ensure_stage(ctx, (size_t)total * req.out_bytes);
+    if (rc != SIEVE_OK) return rc;
+    dst = ctx->d_stage;
+  }
+  CompactParams cp;
+  cp.lo = req.lo;
+  cp.hi = req.hi;
+  cp.k_begin = k_begin;
+  cp.k_end = k_end;
+  cp.L = L;
+  cp.ntiles = ntiles;
+  cp.bitmap = p.bitmap;
+  cp.offsets = offsets;
+  cp.out = dst;
+  cp.cap = req.cap;
+  const int cgrid = (int)std::min<uint64_t>(ntiles, (uint64_t)ctx->num_sms * 4);
+  if (req.out_bytes == 4)
+    compact_kernel<256, uint32_t><<<cgrid, 256, 0, st>>>(cp);
+  else
+    compact_kernel<256, uint64_t><<<cgrid, 256, 0, st>>>(cp);
+  ctx->launches++;
+  SIEVE_CUDA_TRY(cudaGetLastError());
+  if (!dev_out)
+    SIEVE_CUDA_TRY(cudaMemcpyAsync(req.out, dst, (size_t)total * req.out_bytes, cudaMemcpyDeviceToHost, st));
+  SIEVE_CUDA_TRY(cudaStreamSynchronize(st));
+  return SIEVE_OK;
+}
+
+}  // namespace sieve

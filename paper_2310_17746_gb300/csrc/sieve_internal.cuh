@@ -1,0 +1,193 @@
+// sieve_internal.cuh -- context layout and the arithmetic shared by every kernel.
+//
+// Notation follows the paper: a segment ("tile") of the 6k+1 / 6k+5 residue
+// bitmaps (Section 2.1) holds `len` indices per class; index i of class r
+// (r in {1, 5}) stands for the value B + 6 i + r, where B = 6 K0 is the
+// segment's base value.  A base prime P strikes indices id_r, id_r + P, ...
+// (Section 3: adding P to the index adds 6P to the value).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sieve.h"
+
+namespace sieve {
+
+constexpr uint32_t kFullMask = 0xFFFFFFFFu;
+
+// Wheel presieve: the multiples of 5, 7, 11, 13, 17, 19 are removed by
+// copying a periodic pattern instead of striking.  In class-r index space a
+// prime p coprime to 6 repeats with period p, so the joint period is the
+// product of the wheel primes.
+constexpr uint32_t kWheelPeriod = 5u * 7u * 11u * 13u * 17u * 19u;  // 1616615
+constexpr uint32_t kPatternPadWords = 40;  // >= 33 words past the period end
+constexpr uint32_t kPatternWords = (kWheelPeriod + 31) / 32 + kPatternPadWords;
+constexpr uint32_t kFirstSievingPrimeIndex = 8;  // primes[8] == 23 (2,3,5,...,19 before it)
+
+// ---------------------------------------------------------------- arithmetic
+
+__host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
+#ifdef __CUDA_ARCH__
+  return __umul64hi(a, b);
+#else
+  return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+// Division by an invariant divisor d (Granlund & Montgomery, "Division by
+// invariant integers using multiplication", PLDI 1994): with the precomputed
+// reciprocal m = floor((2^64 - 1) / d), q' = floor(n m / 2^64) satisfies
+// q - 1 <= q' <= q for every n < 2^63 (the deficit n (1 + e) / (d 2^64), with
+// e < d the rounding of m, stays below 1/2), so one correction step gives q.
+__host__ __device__ __forceinline__ uint64_t div_invariant(uint64_t n, uint32_t d, uint64_t m) {
+  uint64_t q = mulhi64(n, m);
+  uint64_t r = n - q * (uint64_t)d;
+  if (r >= d) q++;
+  return q;
+}
+
+__host__ __device__ __forceinline__ uint64_t reciprocal64(uint32_t d) { return ~0ull / d; }
+
+// floor(a / 6) for a signed a (so that a - 6 floor(a / 6) is in [0, 6)).
+__host__ __device__ __forceinline__ int64_t floor_div6(int64_t a) {
+  int64_t q = a / 6;
+  if (a - q * 6 < 0) q--;
+  return q;
+}
+
+// Section 3, Table 1, with the P^2 start of Section 2.4.
+//
+// For a segment with base value B (B % 6 == 0) and start value M >= B, and a
+// prime P >= 5 with reciprocal `m`:
+//   M'  = max(M, P^2)                     (start no earlier than P^2)
+//   Q   = greatest multiple of P below M' = floor((M' - 1) / P) * P
+//   q   = Q mod 6,  p = P mod 6 (1 or 5),  R = floor(P / 6)
+//   I   = floor((Q - B) / 6)              (the index "near" Q; may be negative)
+//   id_1 = I + (Table 1 increment for class 1), id_5 likewise.
+// The result indexes the first class-1 / class-5 multiple of P above Q, which
+// is the first one >= M'.  Q - B lies in [-P, segment span), signed 64-bit.
+// Table 1 as coefficients: id_r = I + a_r * R' + b_r, with R' = R when p = 1
+// and R' = R + 1 when p = 5:
+//   p = 1: id_1: q = 0 -> R,      q >= 1 -> (7 - q) R + 1
+//          id_5: q <= 4 -> (5 - q) R,     q = 5 -> 6 R + 1
+//   p = 5: id_1: q = 0 -> 5 R' - 1, q = 1 -> 6 R' - 1, q >= 2 -> (q - 1) R'
+//          id_5: (q + 1) R' - 1
+struct StartIndex {
+  int64_t id1, id5;
+};
+
+__host__ __device__ __forceinline__ StartIndex table1_start(uint64_t B, uint64_t M, uint32_t P,
+                                                            uint64_t m) {
+  uint64_t P2 = (uint64_t)P * P;
+  uint64_t Mp = M > P2 ? M : P2;
+  uint64_t Q = div_invariant(Mp - 1, P, m) * P;
+  int64_t d = (int64_t)(Q - B);
+  int64_t I = floor_div6(d);
+  int32_t q = (int32_t)(d - 6 * I);
+  int32_t R = (int32_t)(P / 6u);
+  int32_t a1, b1, a5, b5, Rp;
+  if (P % 6u == 1u) {
+    Rp = R;
+    a1 = q == 0 ? 1 : 7 - q;
+    b1 = q == 0 ? 0 : 1;
+    a5 = q == 5 ? 6 : 5 - q;
+    b5 = q == 5 ? 1 : 0;
+  } else {
+    Rp = R + 1;
+    a1 = q == 0 ? 5 : (q == 1 ? 6 : q - 1);
+    b1 = q <= 1 ? -1 : 0;
+    a5 = q + 1;
+    b5 = -1;
+  }
+  StartIndex s;
+  s.id1 = I + (int64_t)a1 * Rp + b1;
+  s.id5 = I + (int64_t)a5 * Rp + b5;
+  return s;
+}
+
+// ---------------------------------------------------------------- context
+
+struct DeviceTable {
+  const uint32_t *primes = nullptr;       // device: 2, 3, 5, 7, ... (all primes <= limit)
+  const uint64_t *magic = nullptr;        // device: reciprocal64(primes[i])
+  const uint32_t *host_primes = nullptr;  // host copy of primes
+  uint32_t nprimes = 0;
+  uint64_t limit = 0;
+};
+
+// Number of table primes <= s (host binary search).
+uint32_t host_prime_count_le_table(const DeviceTable &t, uint64_t s);
+
+}  // namespace sieve
+
+struct sieve_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  int smem_optin = 0;          // max dynamic shared memory per block
+  uint64_t max_hi = 0;
+  sieve::DeviceTable table;    // views into the buffers below
+  uint32_t *d_primes = nullptr;
+  uint64_t *d_magic = nullptr;
+  std::vector<uint32_t> h_primes;  // host copy of the base table
+  uint32_t *d_pattern = nullptr;   // class-1 pattern, then class-5 pattern
+  sieve_options opt{};
+  uint64_t launches = 0;
+  // small device scratch: accumulators and status words
+  unsigned long long *d_acc = nullptr;
+  size_t acc_words = 0;
+  // growable device scratch for list mode (bitmaps, tile counts, offsets)
+  void *d_scratch = nullptr;
+  size_t scratch_bytes = 0;
+  // growable device staging for list output bound for host memory
+  void *d_stage = nullptr;
+  size_t stage_bytes = 0;
+  // pinned host staging
+  unsigned long long *h_acc = nullptr;
+};
+
+namespace sieve {
+
+// error reporting (thread-local message)
+void set_error(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define SIEVE_CUDA_TRY(expr)                              \
+  do {                                                    \
+    cudaError_t _e = (expr);                              \
+    if (_e != cudaSuccess) return sieve::cuda_fail(_e, #expr); \
+  } while (0)
+
+// scratch management (api.cu); contents are not preserved when they grow
+int ensure_scratch(sieve_ctx *ctx, size_t bytes);
+int ensure_stage(sieve_ctx *ctx, size_t bytes);
+
+// exact integer square root (host)
+uint64_t isqrt_u64(uint64_t n);
+
+// cudaFuncAttributeMaxDynamicSharedMemorySize for the range kernels (range.cu)
+int range_set_smem_attributes(int bytes);
+
+// Range driver used by the public calls and by the base-table builder
+// (range.cu).  Output kinds for list mode: 4 (uint32) or 8 (uint64) bytes.
+struct RangeRequest {
+  uint64_t lo = 0, hi = 0;
+  int list = 0;              // 0: count only; 1: also write the list
+  int out_bytes = 8;         // list element size
+  void *out = nullptr;       // list output (device or host per out_on_device)
+  size_t cap = 0;
+  int out_on_device = 0;
+  uint64_t seg_width = 0;    // 0: no per-segment counts
+  uint64_t *bins = nullptr;  // per-segment counts (device or host)
+  size_t nbins = 0;
+  sieve_count_result *total = nullptr;  // may be null
+  int async = 0;             // count mode with device outputs: enqueue only
+};
+
+int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req, size_t *n_out);
+
+}  // namespace sieve

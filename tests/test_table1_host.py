@@ -1,0 +1,66 @@
+"""The kernels' Table 1 start-index routine (Section 3), evaluated on the host
+through the C ABI, against the paper's worked example and the plain
+definition (smallest class-r multiple of P that is >= max(M, P^2))."""
+import numpy as np
+import pytest
+
+import oracle
+import oracle_checks as C
+from paper_2310_17746_gb300 import binding
+
+
+def test_worked_example():
+    ex = C.golden("table1_worked_example.json")
+    # the chunk's index 0 is the group base value; M is the chunk start value
+    B = ex["group_base_value"]
+    id1, id5 = binding.table1_start(B, ex["M"], ex["P"])
+    assert (id1, id5) == (ex["id_1"], ex["id_5"])
+    assert B + 6 * id1 + 1 == ex["start_value_1"]
+    assert B + 6 * id5 + 5 == ex["start_value_5"]
+
+
+def _check(B, M, P):
+    id1, id5 = binding.table1_start(B, M, P)
+    assert B + 6 * id1 + 1 == oracle.first_class_multiple(M, P, 1, True), (B, M, P)
+    assert B + 6 * id5 + 5 == oracle.first_class_multiple(M, P, 5, True), (B, M, P)
+
+
+def test_all_twelve_cells_small():
+    """Every (P mod 6, Q mod 6) cell of Table 1, many times over."""
+    primes = [p for p in range(5, 2000) if C.td_is_prime(p)]
+    rng = np.random.default_rng(1)
+    cells = set()
+    for P in primes:
+        for _ in range(12):
+            B = 6 * int(rng.integers(0, 10**6))
+            M = B + int(rng.integers(0, 6 * 4096))
+            _check(B, M, P)
+            Mp = max(M, P * P)
+            cells.add((P % 6, ((Mp - 1) // P * P) % 6))
+    assert len(cells) == 12
+
+
+@pytest.mark.parametrize("scale", [10**12, 10**15, 10**18, 2**62])
+def test_large_values(scale):
+    rng = np.random.default_rng(scale % 1000)
+    big_primes = [4294967291, 3037000493, 2147483647, 1000000007, 999999937, 65521, 23, 29]
+    for P in big_primes:
+        for _ in range(40):
+            B = 6 * (int(rng.integers(0, scale // 6)))
+            M = B + int(rng.integers(0, 6 * (1 << 20)))
+            if M >= 2**63 or max(M, P * P) - B >= 2**62:
+                continue
+            _check(B, M, P)
+
+
+def test_square_start():
+    """Section 2.4: a prime's strikes start at its square (5 -> 25 / 35, 7 -> 49 / 77)."""
+    for P, s1, s5 in ((5, 25, 35), (7, 49, 77), (11, 121, 143), (13, 169, 221)):
+        id1, id5 = binding.table1_start(0, 0, P)
+        assert 6 * id1 + 1 == s1 and 6 * id5 + 5 == s5
+
+
+def test_invalid_arguments():
+    for args in ((1, 1, 7), (0, 0, 4), (0, 0, 9), (12, 6, 7), (0, 0, 3)):
+        with pytest.raises(binding.SieveError):
+            binding.table1_start(*args)
