@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 segmented sieve.
+
+Headline: sieved range width per second for the count of [2, 1e12] with its
+per-2^30-number block histogram (one step = one pass of the whole hot path:
+wheel presieve, Table 1 start offsets, strikes, fix-ups, popcount, checksum,
+histogram).  Under torchrun each rank sieves its own 1e12-wide range (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the CPU oracle on bounded samples of the same workload
+(the only other place this file runs the oracle is the cpu_baseline leg).
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sieved range width/s at n=1e12 (count); batched range queries/s; p99 latency"
+UNIT = "numbers/s"
+WIDTH = 10**12
+SEG_WIDTH = 1 << 30
+PI_1E12 = 37607912018  # published value (OEIS A006880), checked on every run
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def rank_range(rank: int) -> tuple[int, int]:
+    """Rank r sieves a range of width 1e12: rank 0 [2, 1e12], rank r ((r)e12, (r+1)e12]."""
+    if rank == 0:
+        return 2, WIDTH + 1
+    return rank * WIDTH + 1, (rank + 1) * WIDTH + 1
+
+
+# ---------------------------------------------------------------- accounting
+
+def small_primes(n: int):
+    """Primes <= n with a plain numpy sieve (host-side work accounting only)."""
+    import numpy as np
+    a = np.ones(n + 1, dtype=bool)
+    a[:2] = False
+    for i in range(2, int(n**0.5) + 1):
+        if a[i]:
+            a[i * i::i] = False
+    return np.nonzero(a)[0].astype(np.int64)
+
+
+def algorithmic_ops(lo: int, hi: int) -> dict:
+    """Work a segmented 6k+-1 sieve with a {5..19} wheel must do on [lo, hi):
+    strikes = class-1 and class-5 multiples m of each base prime 23 <= p <=
+    isqrt(hi-1) with max(lo, p^2) <= m < hi; words = candidate bits / 32, each
+    written once (presieve) and read once (count)."""
+    import numpy as np
+    s = math.isqrt(hi - 1)
+    p = small_primes(s)
+    p = p[p >= 23]
+    strikes = 0
+    a = np.maximum(lo, p * p)
+    jmax = (hi - 1) // p
+    jmin = (a + p - 1) // p
+    for r in (1, 5):
+        jr = (r * p) % 6           # class-r multiples p*j have j = r*p (mod 6)
+        j0 = jmin + (jr - jmin) % 6
+        cnt = np.where(j0 <= jmax, (jmax - j0) // 6 + 1, 0)
+        strikes += int(cnt.sum())
+    candidates = 2 * ((hi - lo) // 6)
+    words = candidates // 32
+    return {"strikes": strikes, "candidate_words": words, "ops": strikes + 2 * words}
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2310_17746_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_file: str):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel sources
+    are unchanged since it was taken (else None)."""
+    path = os.path.join(ROOT, "profiles", kernel_file)
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_hash") != source_hash():
+        return None
+    return d.get("dram_bytes_per_launch_full")
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.rows: list[list[str]] = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self) -> dict | None:
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_uuid(torch, dev: int):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def oracle_sample(target_s: float, steps: int | None = None):
+    """Time the oracle on 2^30-number blocks spread across [2, 1e12]."""
+    import oracle
+    base = oracle.base_table(10**6)
+    nblocks_total = WIDTH // SEG_WIDTH
+    order = [int(i * 0.6180339887 * nblocks_total) % nblocks_total for i in range(1, 64)]
+    width = 0
+    spent = 0.0
+    times = []
+    for n, b in enumerate(order):
+        lo = max(2, b * SEG_WIDTH)
+        hi = min(WIDTH + 1, (b + 1) * SEG_WIDTH)
+        t = time.perf_counter()
+        oracle.count_range(lo, hi, base=base)
+        dt = time.perf_counter() - t
+        times.append((hi - lo, dt))
+        width += hi - lo
+        spent += dt
+        if steps is None and spent >= target_s:
+            break
+        if steps is not None and n + 1 >= steps:
+            break
+    return width, spent, times, oracle.default_threads()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    # warm-up steps then timed steps, each one 2^30-number block of the workload
+    _, _, _, cores = oracle_sample(0, steps=max(args.warmup, 1))
+    width, spent, times, cores = oracle_sample(0, steps=args.steps)
+    value = width / spent
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * spent / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": "count [2, 1e12] with 2^30-number block histogram",
+                   "sample": f"{len(times)} blocks of 2^30 numbers spread over [2, 1e12], one per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{len(times)} x 2^30-number blocks of [2, 1e12]"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2310_17746_gb300 import binding
+
+    rank, world, local = dist_env()
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    lo, hi = rank_range(rank)
+    stream = torch.cuda.current_stream(dev)
+    sv = binding.Sieve(hi, device=local, stream=stream.cuda_stream)
+    nb = binding.Sieve.nbins(lo, hi, SEG_WIDTH)
+    counts = torch.zeros(nb, dtype=torch.int64, device=dev)
+    total = torch.zeros(2, dtype=torch.int64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)  # 256 MiB > L2
+
+    def step():
+        sv.segment_counts(lo, hi, SEG_WIDTH, counts=counts, total=total, asynchronous=True)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    assert rank != 0 or int(total[0]) == PI_1E12, f"pi(1e12) mismatch: {int(total[0])}"
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(gpu_uuid(torch, local))
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = sv.launch_count()
+    clocks.start()
+    time.sleep(0.25)  # first sample lands inside the timed region
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i)  # evict L2 between steps, outside the timed events
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    barrier()
+    clk = clocks.stop()
+    launches = sv.launch_count() - launches0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_local = sum(step_ms) / 1e3
+    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    widths = sum((rank_range(r)[1] - rank_range(r)[0]) for r in range(world))
+    value = widths * args.steps / t_max
+    got_count = int(total[0])
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    host_counts = np.zeros(nb, dtype=np.uint64)
+    e2e_times = []
+    for i in range(min(args.steps, 3)):
+        flush.fill_(i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tot_host, _ = sv.segment_counts(lo, hi, SEG_WIDTH, counts=host_counts)
+        e2e_times.append(time.perf_counter() - t0)
+    assert rank != 0 or tot_host.count == PI_1E12
+    e2e_local = statistics.mean(e2e_times)
+    te = torch.tensor([e2e_local], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = widths / float(te.item())
+
+    if rank != 0:
+        sv.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel (the tile sieve; one launch per step)
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0)
+    alg = algorithmic_ops(lo, hi)
+    per_launch_s = t_local / args.steps
+    achieved = alg["ops"] / per_launch_s / 1e9
+    peak = props.multi_processor_count * 32 * sm_max * 1e6 / 1e9
+    opts = sv.options()
+    traffic = profiled_traffic("range_tiles_count_1e12.json")
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        w, spent, times, cores = oracle_sample(args.cpu_seconds)
+        cpu = {"value": w / spent, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{len(times)} blocks of 2^30 numbers spread over [2, 1e12] ({w:.3e} numbers, {spent:.1f} s)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "count [2, 1e12] with 2^30-number block histogram (932 bins); "
+                               "rank r>0 sieves (r*1e12, (r+1)*1e12]",
+                   "lo": lo, "hi_exclusive": hi, "seg_width": SEG_WIDTH,
+                   "tile_bits": opts["tile_bits"], "block_threads": opts["block_threads"],
+                   "group_hits": opts["group_hits"],
+                   "l2": "flushed between steps (256 MiB write outside the timed events)"},
+        "check": {"pi_1e12": got_count, "expected": PI_1E12, "ok": got_count == PI_1E12},
+        "roofline": {"bound": "alu", "resource": "SM shared-memory read-modify-write lane ops "
+                                                  "(one 32-lane shared access per SM per clock)",
+                     "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
+                     "traffic": traffic, "kernel": "range_tiles_kernel",
+                     "ops_per_launch": alg["ops"], "strikes_per_launch": alg["strikes"],
+                     "peak_basis": f"{props.multi_processor_count} SMs x 32 lanes x {sm_max:.0f} MHz "
+                                   f"({'measured' if peaks else 'fallback'} max SM clock)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16,
+                "d2h_bytes_per_step": 8 * nb + 16},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "wall_s_timed": wall,
+    }
+    print(json.dumps(line), flush=True)
+    sv.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(BLOCK) range_tiles_kernel(const RangeKernelPar
     __syncthreads();
 
     const ValidRange v = valid_range(p.lo, p.hi, B, len);
-    fixup_tile<BLOCK>(s1, s5, nwords, K0, v);
+    fixup_tile<BLOCK>(s1, s5, len, nwords, K0, v);
     __syncthreads();
 
     // popcount, checksum, and the count below the segment boundary (if any)

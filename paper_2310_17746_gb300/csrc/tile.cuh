@@ -140,15 +140,19 @@ __device__ __forceinline__ ValidRange valid_range(uint64_t lo, uint64_t hi, uint
 }
 
 // Fix-ups after striking (Section 2.1: the arrays hold candidates > 3):
-//   * tile at value 0: clear the value 1, restore the wheel primes 5..19
-//     (the presieve pattern removed them with their multiples);
+//   * tiles holding values below 24: clear the value 1, restore the wheel
+//     primes 5..19 (the presieve pattern removed them with their multiples);
 //   * edge tiles: clear the bits outside [lo, hi) and past len.
 template <int BLOCK>
-__device__ __forceinline__ void fixup_tile(uint32_t *s1, uint32_t *s5, uint32_t nwords, uint64_t K0,
-                                           const ValidRange &v) {
-  if (K0 == 0 && threadIdx.x == 0) {
-    s1[0] = (s1[0] & ~1u) | 0xEu;  // 1 out; 7, 13, 19 in
-    s5[0] |= 0x7u;                 // 5, 11, 17 in
+__device__ __forceinline__ void fixup_tile(uint32_t *s1, uint32_t *s5, uint32_t len, uint32_t nwords,
+                                           uint64_t K0, const ValidRange &v) {
+  if (K0 < 4 && threadIdx.x == 0) {  // the tile holds values below 24
+    if (K0 == 0) s1[0] &= ~1u;       // 1 is not a prime
+    const uint32_t wheel[6] = {5, 7, 11, 13, 17, 19};
+    for (int q = 0; q < 6; q++) {
+      const uint32_t wv = wheel[q], r = wv % 6, k = wv / 6;
+      if (k >= K0 && k - K0 < len) (r == 1 ? s1 : s5)[(k - K0) >> 5] |= 1u << ((k - K0) & 31);
+    }
   }
   __syncthreads();
   const int64_t full = 32 * (int64_t)nwords;

@@ -49,7 +49,10 @@ def test_random_small_ranges(sv):
 def test_prime_square_boundaries(sv):
     """Ranges that start or end at p^2, p^2 + 1 for base primes p (first strikes)."""
     for p in (23, 29, 31, 97, 101, 1009, 7919, 65521, 99991, 999983):
-        for lo, hi in ((p * p, p * p + 1), (p * p - 1, p * p + 2), (p * p - 100, p * p), (p, p * p + 1000)):
+        cases = [(p * p, p * p + 1), (p * p - 1, p * p + 2), (p * p - 100, p * p), (p * p - 6001, p * p + 7001)]
+        if p < 5000:
+            cases.append((p, p * p + 1000))
+        for lo, hi in cases:
             want = oracle.count_range(lo, hi, base=_oracle_base(hi))
             r = sv.range_count(lo, hi)
             assert (r.count, r.checksum) == want, (p, lo, hi)
@@ -106,7 +109,7 @@ def test_segment_counts_odd_widths(sv):
         assert np.array_equal(bins, obins), (lo, hi, w)
 
 
-@pytest.mark.parametrize("tile_bits", [1024, 4096, 32768, 1 << 18, 1 << 20])
+@pytest.mark.parametrize("tile_bits", [1024, 4096, 32768, 3 << 17, 1 << 19])
 @pytest.mark.parametrize("threads", [256, 512, 1024])
 def test_option_sweep(sv, tile_bits, threads):
     old = sv.options()
@@ -159,5 +162,7 @@ def test_errors(sv):
         sv.segment_counts(0, 10**6, 100)  # width below the minimum
     with pytest.raises(binding.SieveError):
         sv.set_options(tile_bits=1000)
+    with pytest.raises(binding.SieveError):
+        sv.set_options(tile_bits=1 << 20)  # 256 KB of bitmaps do not fit in shared memory
     r = sv.range_count(77, 77)
     assert (r.count, r.checksum) == (0, 0)
