@@ -49,7 +49,7 @@ def test_random_small_ranges(sv):
 def test_prime_square_boundaries(sv):
     """Ranges that start or end at p^2, p^2 + 1 for base primes p (first strikes)."""
     for p in (23, 29, 31, 97, 101, 1009, 7919, 65521, 99991, 999983):
-        cases = [(p * p, p * p + 1), (p * p - 1, p * p + 2), (p * p - 100, p * p), (p * p - 6001, p * p + 7001)]
+        cases = [(p * p, p * p + 1), (p * p - 1, p * p + 2), (p * p - 100, p * p), (max(0, p * p - 6001), p * p + 7001)]
         if p < 5000:
             cases.append((p, p * p + 1000))
         for lo, hi in cases:
