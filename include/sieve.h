@@ -85,7 +85,10 @@ typedef struct {
   uint32_t ctas_per_sm;    /* resident CTAs per SM the launch aims for (0: as many as fit)   */
   uint32_t group_hits;     /* a prime is struck by a group of lanes when it has at least this
                               many hits per lane in a segment; below that, one lane per prime */
-  uint32_t reserved[4];
+  uint32_t presieve_groups;  /* 0..8: besides the wheel {5..19}, how many groups of three
+                              primes (23, 29, 31), (37, 41, 43), ... up to 131 are removed by
+                              copying periodic patterns instead of striking                  */
+  uint32_t reserved[3];
 } sieve_options;
 
 /* ---------------------------------------------------------------- context */

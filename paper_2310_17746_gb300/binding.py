@@ -50,11 +50,12 @@ class CountResult(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("tile_bits", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
                 ("ctas_per_sm", ctypes.c_uint32), ("group_hits", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 4)]
+                ("presieve_groups", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
 
     def as_dict(self) -> dict:
         return {"tile_bits": self.tile_bits, "block_threads": self.block_threads,
-                "ctas_per_sm": self.ctas_per_sm, "group_hits": self.group_hits}
+                "ctas_per_sm": self.ctas_per_sm, "group_hits": self.group_hits,
+                "presieve_groups": self.presieve_groups}
 
 
 _u64 = ctypes.c_uint64

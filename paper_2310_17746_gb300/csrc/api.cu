@@ -74,29 +74,34 @@ int ensure_stage(sieve_ctx *ctx, size_t bytes) {
   return SIEVE_OK;
 }
 
-// Wheel pattern: bit k (k mod period) of class r is 1 iff 6k + r has no
-// factor among the wheel primes.  Extended past the period so that any
-// 32-word window starting below the period can be read without wrapping.
-__global__ void wheel_pattern_kernel(uint32_t *pat) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= kPatternWords) return;
+// Presieve pattern g in the sliced layout for tiles of W words per class: word
+// j holds, at bit b, whether 6 x + r (x = (j + b W) mod period) has no factor
+// among the pattern's primes.  Words run to period + W so that a tile's W
+// words starting at any phase below the period are contiguous.
+struct SlicedGenArgs {
+  uint32_t period, W, words, off1, off5;
+  uint32_t primes[6];  // 0 = unused
+};
+
+__global__ void sliced_pattern_kernel(uint32_t *pat, const SlicedGenArgs a) {
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.words) return;
   uint32_t w1 = 0, w5 = 0;
-  for (uint32_t j = 0; j < 32; j++) {
-    uint32_t k = 32 * i + j;
-    while (k >= kWheelPeriod) k -= kWheelPeriod;
-    const uint32_t v1 = 6 * k + 1, v5 = 6 * k + 5;
-    const uint32_t wheel[6] = {5, 7, 11, 13, 17, 19};
+  for (uint32_t b = 0; b < 32; b++) {
+    const uint32_t x = (uint32_t)(((uint64_t)j + (uint64_t)b * a.W) % a.period);
+    const uint64_t v1 = 6ull * x + 1, v5 = 6ull * x + 5;
     bool c1 = true, c5 = true;
 #pragma unroll
     for (int q = 0; q < 6; q++) {
-      c1 = c1 && (v1 % wheel[q] != 0);
-      c5 = c5 && (v5 % wheel[q] != 0);
+      if (a.primes[q] == 0) continue;
+      c1 = c1 && (v1 % a.primes[q] != 0);
+      c5 = c5 && (v5 % a.primes[q] != 0);
     }
-    w1 |= (uint32_t)c1 << j;
-    w5 |= (uint32_t)c5 << j;
+    w1 |= (uint32_t)c1 << b;
+    w5 |= (uint32_t)c5 << b;
   }
-  pat[i] = w1;
-  pat[kPatternWords + i] = w5;
+  pat[a.off1 + j] = w1;
+  pat[a.off5 + j] = w5;
 }
 
 __global__ void reciprocal_kernel(const uint32_t *__restrict__ primes, uint64_t *__restrict__ magic, uint32_t n) {
@@ -126,6 +131,51 @@ static uint64_t pi_upper(uint64_t x) {
   return (uint64_t)(1.25506 * (double)x / lx) + 64;
 }
 
+int sliced_patterns(sieve_ctx *ctx, uint32_t logW, const uint32_t **ptr, PatternDesc *pd) {
+  if (logW >= 32) {
+    set_error("tile width out of range");
+    return SIEVE_ERR_INVALID;
+  }
+  auto &ss = ctx->sliced[logW];
+  if (!ss.d) {
+    const uint32_t W = 1u << logW;
+    uint64_t total = 0;
+    PatternDesc d[kNumPatterns];
+    for (int g = 0; g < kNumPatterns; g++) {
+      const uint32_t words = pattern_period(g) + W + 32;
+      d[g].period = pattern_period(g);
+      d[g].off1 = (uint32_t)total;
+      d[g].off5 = (uint32_t)(total + words);
+      d[g].pad_ = 0;
+      d[g].magic = reciprocal64(pattern_period(g));
+      total += 2ull * words;
+    }
+    uint32_t *buf = nullptr;
+    SIEVE_CUDA_TRY(cudaMalloc(&buf, total * sizeof(uint32_t)));
+    for (int g = 0; g < kNumPatterns; g++) {
+      SlicedGenArgs a;
+      a.period = d[g].period;
+      a.W = W;
+      a.words = d[g].period + W + 32;
+      a.off1 = d[g].off1;
+      a.off5 = d[g].off5;
+      for (int q = 0; q < 6; q++) a.primes[q] = kPatternPrimes[g][q];
+      sliced_pattern_kernel<<<(a.words + 255) / 256, 256, 0, ctx->stream>>>(buf, a);
+      ctx->launches++;
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) {
+        cudaFree(buf);
+        return cuda_fail(e, "sliced_pattern_kernel");
+      }
+    }
+    ss.d = buf;
+    for (int g = 0; g < kNumPatterns; g++) ss.pd[g] = d[g];
+  }
+  *ptr = ss.d;
+  for (int g = 0; g < kNumPatterns; g++) pd[g] = ss.pd[g];
+  return SIEVE_OK;
+}
+
 }  // namespace sieve
 
 using namespace sieve;
@@ -136,7 +186,7 @@ static void free_ctx(sieve_ctx *c) {
   if (!c) return;
   cudaFree(c->d_primes);
   cudaFree(c->d_magic);
-  cudaFree(c->d_pattern);
+  for (auto &ss : c->sliced) cudaFree(ss.d);
   cudaFree(c->d_acc);
   cudaFree(c->d_scratch);
   cudaFree(c->d_stage);
@@ -147,16 +197,17 @@ static void free_ctx(sieve_ctx *c) {
 static sieve_options default_options() {
   sieve_options o;
   memset(&o, 0, sizeof(o));
-  o.tile_bits = 1u << 18;
-  o.block_threads = 512;
+  o.tile_bits = 1u << 19;
+  o.block_threads = 1024;
   o.ctas_per_sm = 0;
-  o.group_hits = 2;
+  o.group_hits = 4;
+  o.presieve_groups = 2;
   return o;
 }
 
 static int validate_options(const sieve_ctx *c, const sieve_options &o) {
-  if (o.tile_bits < 1024 || o.tile_bits % 1024 || o.tile_bits > (1u << 20)) {
-    set_error("tile_bits must be a multiple of 1024 in [1024, 2^20]");
+  if (o.tile_bits < 1024 || (o.tile_bits & (o.tile_bits - 1)) || o.tile_bits > (1u << 20)) {
+    set_error("tile_bits must be a power of two in [1024, 2^19]");
     return SIEVE_ERR_INVALID;
   }
   if ((int)(o.tile_bits / 4) > c->smem_optin) {
@@ -174,6 +225,10 @@ static int validate_options(const sieve_ctx *c, const sieve_options &o) {
   }
   if (o.group_hits == 0 || o.group_hits > 1024) {
     set_error("group_hits must be in [1, 1024]");
+    return SIEVE_ERR_INVALID;
+  }
+  if (o.presieve_groups > (uint32_t)kMaxPresieveGroups) {
+    set_error("presieve_groups must be in [0, %d]", kMaxPresieveGroups);
     return SIEVE_ERR_INVALID;
   }
   return SIEVE_OK;
@@ -272,15 +327,8 @@ extern "C" int sieve_create(sieve_ctx **ctx, uint64_t max_hi, int device, void *
     while (c->opt.tile_bits / 4 > (uint32_t)c->smem_optin) c->opt.tile_bits /= 2;
     c->acc_words = 16;
     if ((e = cudaMalloc(&c->d_acc, c->acc_words * sizeof(unsigned long long))) != cudaSuccess ||
-        (e = cudaMallocHost(&c->h_acc, c->acc_words * sizeof(unsigned long long))) != cudaSuccess ||
-        (e = cudaMalloc(&c->d_pattern, 2 * kPatternWords * sizeof(uint32_t))) != cudaSuccess) {
+        (e = cudaMallocHost(&c->h_acc, c->acc_words * sizeof(unsigned long long))) != cudaSuccess) {
       rc = cuda_fail(e, "context allocation");
-      break;
-    }
-    wheel_pattern_kernel<<<(kPatternWords + 255) / 256, 256, 0, c->stream>>>(c->d_pattern);
-    c->launches++;
-    if ((e = cudaGetLastError()) != cudaSuccess) {
-      rc = cuda_fail(e, "wheel_pattern_kernel");
       break;
     }
     const uint64_t limit = std::max<uint64_t>(isqrt_u64(max_hi - 1), 1u << 16);
@@ -477,6 +525,13 @@ extern "C" int sieve_table1_start(uint64_t B, uint64_t M, uint32_t P, int64_t *i
   if (Mp - B >= (1ull << 62)) {
     set_error("sieve_table1_start: max(M, P^2) - B too large");
     return SIEVE_ERR_INVALID;
+  }
+  if (M == B) {  // the tile case the kernels evaluate
+    uint64_t k1, k5;
+    tile_starts(B, P, reciprocal64(P), k1, k5);
+    *id1 = (int64_t)k1;
+    *id5 = (int64_t)k5;
+    return SIEVE_OK;
   }
   StartIndex s = table1_start(B, M, P, reciprocal64(P));
   *id1 = s.id1;

@@ -18,13 +18,17 @@ struct RangeKernelParams {
   uint64_t lo, hi;          // [lo, hi)
   uint64_t k_begin;         // class index of tile 0's index 0
   uint64_t k_end;           // ceil((hi - 1) / 6): indices below it can hold a value < hi
-  uint32_t L;               // indices per class per tile (multiple of 32)
+  uint32_t L;               // indices per class per tile (32 W, W a power of two)
+  uint32_t logW;            // log2(L / 32)
   uint32_t ntiles;
   const uint32_t *primes;
   const uint64_t *magic;
   uint32_t nprimes;         // primes[0..nprimes) cover isqrt(hi - 1)
+  uint32_t i_first;         // first prime index struck (after the presieved ones)
   uint32_t i_split;         // primes with index < i_split are struck by a warp
-  const uint32_t *pattern;  // wheel pattern, class 1 then class 5
+  const uint32_t *sliced;   // presieve patterns in the sliced layout for this W
+  PatternDesc pd[kNumPatterns];
+  int npat;                 // patterns in use (wheel + groups)
   // count-mode outputs (atomically accumulated)
   unsigned long long *count;
   unsigned long long *checksum;
@@ -37,12 +41,14 @@ struct RangeKernelParams {
 };
 
 template <int BLOCK, bool LIST>
-__global__ void __launch_bounds__(BLOCK) range_tiles_kernel(const RangeKernelParams p) {
+__global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const RangeKernelParams p) {
   constexpr int NWARPS = BLOCK / 32;
   extern __shared__ uint32_t smem[];
+  const uint32_t W = p.L / 32;
   uint32_t *s1 = smem;
-  uint32_t *s5 = smem + p.L / 32;
-  __shared__ uint32_t sh_np;
+  uint32_t *s5 = smem + W;
+  uint2 *starts = (uint2 *)(smem + 2 * W);  // warp-band start indices
+  __shared__ uint32_t sh_np, sh_next;
   __shared__ uint64_t sh_bin0;
   __shared__ int64_t sh_t1, sh_t5;
   __shared__ int sh_has_boundary;
@@ -52,10 +58,12 @@ __global__ void __launch_bounds__(BLOCK) range_tiles_kernel(const RangeKernelPar
   for (uint32_t t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
     const uint64_t K0 = p.k_begin + (uint64_t)t * p.L;
     const uint64_t left = p.k_end - K0;
-    const uint32_t len = left < p.L ? (uint32_t)left : p.L;
-    const uint32_t nwords = (len + 31) / 32;
+    TileGeom tg;
+    tg.W = W;
+    tg.logW = p.logW;
+    tg.len = left < p.L ? (uint32_t)left : p.L;
     const uint64_t B = 6 * K0;
-    const uint64_t tile_end = B + 6ull * len;
+    const uint64_t tile_end = B + 6ull * tg.len;
     const uint64_t vend = tile_end < p.hi ? tile_end : p.hi;
 
     if (warp == 0) {
@@ -64,6 +72,7 @@ __global__ void __launch_bounds__(BLOCK) range_tiles_kernel(const RangeKernelPar
       const uint32_t np = warp_count_le(p.primes, p.nprimes, s);
       if (lane == 0) {
         sh_np = np;
+        sh_next = p.i_first;
         sh_has_boundary = 0;
         if (p.seg_width) {
           const uint64_t v0 = B > p.lo ? B : p.lo;
@@ -73,38 +82,39 @@ __global__ void __launch_bounds__(BLOCK) range_tiles_kernel(const RangeKernelPar
           if (X < vend) {
             sh_has_boundary = 1;
             int64_t t1 = ceil_div6((int64_t)(X - B) - 1), t5 = ceil_div6((int64_t)(X - B) - 5);
-            sh_t1 = t1 < 0 ? 0 : (t1 > (int64_t)len ? (int64_t)len : t1);
-            sh_t5 = t5 < 0 ? 0 : (t5 > (int64_t)len ? (int64_t)len : t5);
+            sh_t1 = t1 < 0 ? 0 : (t1 > (int64_t)tg.len ? (int64_t)tg.len : t1);
+            sh_t5 = t5 < 0 ? 0 : (t5 > (int64_t)tg.len ? (int64_t)tg.len : t5);
           }
         }
       }
     }
-    presieve_copy<NWARPS>(s1, s5, nwords, K0, p.pattern);
+    presieve_copy<BLOCK>(s1, s5, tg, K0, p.sliced, p.pd, p.npat);
+    warp_band_starts<BLOCK>(starts, B, tg.len, p.primes, p.magic, p.i_first, p.i_split);
     __syncthreads();
 
-    strike_primes<BLOCK>(s1, s5, B, len, p.primes, p.magic, kFirstSievingPrimeIndex, p.i_split, sh_np);
+    strike_primes<BLOCK>(s1, s5, B, tg, p.primes, p.magic, starts, p.i_first, p.i_split, sh_np, &sh_next);
     __syncthreads();
 
-    const ValidRange v = valid_range(p.lo, p.hi, B, len);
-    fixup_tile<BLOCK>(s1, s5, len, nwords, K0, v);
+    const ValidRange v = valid_range(p.lo, p.hi, B, tg.len);
+    fixup_tile<BLOCK>(s1, s5, tg, K0, v, p.npat);
     __syncthreads();
 
-    // popcount, checksum, and the count below the segment boundary (if any)
+    // popcount, checksum, and the count below the segment boundary (if any).
+    // Word w holds indices w + b W: their values sum to
+    // popc * (6 (K0 + w) + r) + 6 W * (sum of the set bit positions b).
     uint64_t cnt = 0, sum = 0, below = 0;
     const int has_b = sh_has_boundary;
     const int64_t t1 = has_b ? sh_t1 : 0, t5 = has_b ? sh_t5 : 0;
-    for (uint32_t w = threadIdx.x; w < nwords; w += BLOCK) {
+    for (uint32_t w = threadIdx.x; w < W; w += BLOCK) {
       const uint32_t a = s1[w], b = s5[w];
-      if (LIST) p.bitmap[(uint64_t)t * (p.L / 32) + w] = make_uint2(a, b);
+      if (LIST) p.bitmap[(uint64_t)t * W + w] = make_uint2(a, b);
       const uint32_t ca = __popc(a), cb = __popc(b);
       cnt += ca + cb;
-      const uint64_t vb = 6 * (K0 + 32ull * w);
+      const uint64_t vb = 6 * (K0 + w);
       sum += (uint64_t)ca * (vb + 1) + (uint64_t)cb * (vb + 5) +
-             6ull * (uint64_t)(bit_index_sum(a) + bit_index_sum(b));
-      if (has_b) {
-        const int64_t base = 32 * (int64_t)w;
-        below += __popc(a & bit_range_mask(0, t1 - base)) + __popc(b & bit_range_mask(0, t5 - base));
-      }
+             6ull * W * (uint64_t)(bit_index_sum(a) + bit_index_sum(b));
+      if (has_b)
+        below += __popc(a & below_mask(t1, w, tg.logW, W)) + __popc(b & below_mask(t5, w, tg.logW, W));
     }
     block_sum3<BLOCK>(cnt, sum, below, red);
     if (threadIdx.x == 0) {
@@ -175,17 +185,21 @@ __global__ void __launch_bounds__(BLOCK) scan_tile_counts_kernel(const uint32_t 
 
 struct CompactParams {
   uint64_t lo, hi, k_begin, k_end;
-  uint32_t L, ntiles;
-  const uint2 *bitmap;
+  uint32_t L, logW, ntiles;
+  const uint2 *bitmap;      // per tile W (class-1 word, class-5 word) pairs, sliced layout
   const uint64_t *offsets;  // ntiles + 1 entries; offsets[ntiles] = total
   void *out;
   uint64_t cap;
 };
 
-// List compaction: per tile, each warp owns a contiguous run of words; a
-// first pass counts the warp's primes, a block scan places the warps, a
-// second pass interleaves class-1 / class-5 bits in value order, scans the
-// lanes' counts with shuffles and writes the values.
+// List compaction in value order.  In the sliced layout row b of a tile is
+// the index run [b W, b W + W); a unit (b, c) is the 32 indices b W + 32 c + j,
+// j = 0..31, and units in row-major order are in value order.  A warp reads
+// the 32 words of chunk c and extracts row b of each class with one ballot
+// (the ballot transposes the bits), interleaves the two classes in value
+// order and lane j writes the values of bits 2j and 2j+1.  Each warp owns a
+// contiguous run of units; a first pass counts them and a block scan places
+// the warps.
 template <int BLOCK, typename OutT>
 __global__ void __launch_bounds__(BLOCK) compact_kernel(const CompactParams p) {
   constexpr int NWARPS = BLOCK / 32;
@@ -193,12 +207,15 @@ __global__ void __launch_bounds__(BLOCK) compact_kernel(const CompactParams p) {
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (p.offsets[p.ntiles] > p.cap) return;  // capacity: the host reports it
   OutT *out = (OutT *)p.out;
+  const uint32_t W = p.L / 32;
+  const uint32_t chunk_bits = p.logW - 5;  // chunks per row = W / 32
   for (uint32_t t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
     const uint64_t K0 = p.k_begin + (uint64_t)t * p.L;
     const uint64_t left = p.k_end - K0;
     const uint32_t len = left < p.L ? (uint32_t)left : p.L;
-    const uint32_t nwords = (len + 31) / 32;
-    const uint2 *bm = p.bitmap + (uint64_t)t * (p.L / 32);
+    const uint32_t rows = (len + W - 1) >> p.logW;
+    const uint32_t units = rows << chunk_bits;
+    const uint2 *bm = p.bitmap + (uint64_t)t * W;
     uint64_t off = p.offsets[t];
     if (K0 == 0) {  // 2 and 3 first
       if (threadIdx.x == 0) {
@@ -208,17 +225,15 @@ __global__ void __launch_bounds__(BLOCK) compact_kernel(const CompactParams p) {
       }
       off += (p.lo <= 2 && 2 < p.hi) + (p.lo <= 3 && 3 < p.hi);
     }
-    uint32_t per_warp = (nwords + NWARPS - 1) / NWARPS;
-    per_warp = (per_warp + 31) & ~31u;
-    const uint32_t w_begin = warp * per_warp;
-    const uint32_t w_end = min(w_begin + per_warp, nwords);
+    const uint32_t per_warp = (units + NWARPS - 1) / NWARPS;
+    const uint32_t u_begin = min(warp * per_warp, units);
+    const uint32_t u_end = min(u_begin + per_warp, units);
     uint32_t c = 0;
-    for (uint32_t w = w_begin + lane; w < w_end; w += 32) {
+    for (uint32_t u = u_begin; u < u_end; u++) {
+      const uint32_t b = u >> chunk_bits, w = ((u & ((1u << chunk_bits) - 1)) << 5) + lane;
       const uint2 x = bm[w];
-      c += __popc(x.x) + __popc(x.y);
+      c += __popc(__ballot_sync(kFullMask, (x.x >> b) & 1u)) + __popc(__ballot_sync(kFullMask, (x.y >> b) & 1u));
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFullMask, c, o);
     if (lane == 0) warp_base[warp] = c;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -231,28 +246,17 @@ __global__ void __launch_bounds__(BLOCK) compact_kernel(const CompactParams p) {
     }
     __syncthreads();
     uint64_t base = warp_base[warp];
-    for (uint32_t w0 = w_begin; w0 < w_end; w0 += 32) {
-      const uint32_t w = w0 + lane;
-      uint64_t z = 0;
-      if (w < w_end) {
-        const uint2 x = bm[w];
-        z = interleave_classes(x.x, x.y);
-      }
-      const uint32_t n = __popcll(z);
-      uint32_t incl = n;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(kFullMask, incl, o);
-        if (lane >= (uint32_t)o) incl += y;
-      }
-      uint64_t pos = base + incl - n;
-      const uint64_t vb = 6 * (K0 + 32ull * w);
-      while (z) {
-        const uint32_t j = __ffsll((long long)z) - 1;
-        z &= z - 1;
-        out[pos++] = (OutT)(vb + 6ull * (j >> 1) + ((j & 1) ? 5u : 1u));
-      }
-      base += __shfl_sync(kFullMask, incl, 31);
+    for (uint32_t u = u_begin; u < u_end; u++) {
+      const uint32_t b = u >> chunk_bits, c0 = (u & ((1u << chunk_bits) - 1)) << 5;
+      const uint2 x = bm[c0 + lane];
+      const uint32_t m1 = __ballot_sync(kFullMask, (x.x >> b) & 1u);
+      const uint32_t m5 = __ballot_sync(kFullMask, (x.y >> b) & 1u);
+      const uint64_t z = interleave_classes(m1, m5);
+      const uint64_t vb = 6 * (K0 + ((uint64_t)b << p.logW) + c0 + lane);
+      const uint32_t q1 = 2 * lane, q5 = 2 * lane + 1;
+      if ((z >> q1) & 1ull) out[base + __popcll(z & ((1ull << q1) - 1))] = (OutT)(vb + 1);
+      if ((z >> q5) & 1ull) out[base + __popcll(z & ((1ull << q5) - 1))] = (OutT)(vb + 5);
+      base += __popcll(z);
     }
     __syncthreads();
   }
@@ -319,8 +323,18 @@ int range_set_smem_attributes(int bytes) {
   return set_smem_attr<1024>(bytes);
 }
 
-// Largest multiple of 32 that is <= x.
-static uint32_t floor32(uint64_t x) { return (uint32_t)(x & ~31ull); }
+// Largest power of two <= x (x >= 1).
+static uint32_t floor_pow2(uint64_t x) {
+  uint32_t r = 1;
+  while ((uint64_t)r * 2 <= x && r < (1u << 30)) r *= 2;
+  return r;
+}
+
+static uint32_t log2u(uint32_t x) {
+  uint32_t r = 0;
+  while ((1u << r) < x) r++;
+  return r;
+}
 
 int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req, size_t *n_out) {
   if (n_out) *n_out = 0;
@@ -373,7 +387,7 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
   const int threads = (int)ctx->opt.block_threads;
   uint32_t L = ctx->opt.tile_bits;
   if (req.seg_width) {  // at most one segment boundary per tile: 6 L <= seg_width
-    const uint32_t lw = floor32(req.seg_width / 6);
+    const uint32_t lw = floor_pow2(req.seg_width / 6);
     if (lw < L) L = lw;
   }
   size_t smem = (size_t)L / 4;
@@ -388,9 +402,11 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
   const uint64_t slots = (uint64_t)ctx->num_sms * (uint64_t)per_sm;
   // small ranges: shrink tiles so that every CTA slot gets work
   if (span > 0 && span < (uint64_t)L * slots) {
-    uint64_t want = (span + slots - 1) / slots;
-    want = (want + 1023) / 1024 * 1024;
-    if (want < L) L = (uint32_t)want;
+    const uint64_t want = (span + slots - 1) / slots;
+    uint32_t lw = floor_pow2(want);
+    if (lw < want) lw *= 2;
+    if (lw < 1024) lw = 1024;
+    if (lw < L) L = lw;
     smem = (size_t)L / 4;
   }
   const uint64_t ntiles64 = span ? (span + L - 1) / L : 0;
@@ -405,7 +421,15 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
   // >= group_hits hits per lane in a tile, i.e. P <= L / (32 * group_hits)
   const uint32_t np = host_prime_count_le_table(table, s);
   const uint64_t gmax = L / (32ull * std::max<uint32_t>(1u, ctx->opt.group_hits));
-  const uint32_t i_split = host_prime_count_le_table(table, gmax);
+  const uint32_t i_first = first_struck_prime_index((int)ctx->opt.presieve_groups);
+  uint32_t i_split = std::min(host_prime_count_le_table(table, gmax), np);
+  if (i_split < i_first) i_split = i_first;
+  smem += (size_t)(i_split - i_first) * sizeof(uint2);
+  if (smem > (size_t)ctx->smem_optin) {
+    set_error("tile of %u bits with %u warp-band primes needs %zu bytes of shared memory", L, i_split - i_first,
+              smem);
+    return SIEVE_ERR_INVALID;
+  }
 
   RangeKernelParams p;
   memset(&p, 0, sizeof(p));
@@ -414,12 +438,16 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
   p.k_begin = k_begin;
   p.k_end = k_end;
   p.L = L;
+  p.logW = log2u(L / 32);
   p.ntiles = ntiles;
   p.primes = table.primes;
   p.magic = table.magic;
   p.nprimes = np;
   p.i_split = i_split;
-  p.pattern = ctx->d_pattern;
+  p.i_first = i_first;
+  p.npat = 1 + (int)ctx->opt.presieve_groups;
+  rc = sliced_patterns(ctx, p.logW, &p.sliced, p.pd);
+  if (rc != SIEVE_OK) return rc;
   p.seg_width = req.seg_width;
   p.first_seg = req.seg_width ? req.lo / req.seg_width : 0;
 
@@ -528,6 +556,7 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
   cp.k_begin = k_begin;
   cp.k_end = k_end;
   cp.L = L;
+  cp.logW = p.logW;
   cp.ntiles = ntiles;
   cp.bitmap = p.bitmap;
   cp.offsets = offsets;

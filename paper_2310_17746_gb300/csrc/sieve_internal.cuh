@@ -19,14 +19,42 @@ namespace sieve {
 
 constexpr uint32_t kFullMask = 0xFFFFFFFFu;
 
-// Wheel presieve: the multiples of 5, 7, 11, 13, 17, 19 are removed by
-// copying a periodic pattern instead of striking.  In class-r index space a
-// prime p coprime to 6 repeats with period p, so the joint period is the
-// product of the wheel primes.
+// Presieve: the multiples of the smallest base primes are removed by copying
+// periodic bit patterns into a tile instead of striking them one by one.  In
+// class-r index space a prime p coprime to 6 repeats with period p, so a group
+// of primes repeats with the product of its members.  Pattern 0 is the wheel
+// {5, 7, 11, 13, 17, 19}; patterns 1..kMaxPresieveGroups are groups of three
+// consecutive primes from 23 on.  A context presieves with the wheel and the
+// first `presieve_groups` groups; the strike loop starts after the last
+// presieved prime.
+constexpr int kMaxPresieveGroups = 8;
+constexpr int kNumPatterns = 1 + kMaxPresieveGroups;
+constexpr uint32_t kPatternPadWords = 40;  // >= 33 words past each period end
 constexpr uint32_t kWheelPeriod = 5u * 7u * 11u * 13u * 17u * 19u;  // 1616615
-constexpr uint32_t kPatternPadWords = 40;  // >= 33 words past the period end
-constexpr uint32_t kPatternWords = (kWheelPeriod + 31) / 32 + kPatternPadWords;
-constexpr uint32_t kFirstSievingPrimeIndex = 8;  // primes[8] == 23 (2,3,5,...,19 before it)
+// the primes of each pattern (0-padded)
+constexpr uint32_t kPatternPrimes[kNumPatterns][6] = {
+    {5, 7, 11, 13, 17, 19}, {23, 29, 31, 0, 0, 0},    {37, 41, 43, 0, 0, 0},
+    {47, 53, 59, 0, 0, 0},  {61, 67, 71, 0, 0, 0},    {73, 79, 83, 0, 0, 0},
+    {89, 97, 101, 0, 0, 0}, {103, 107, 109, 0, 0, 0}, {113, 127, 131, 0, 0, 0}};
+constexpr uint32_t pattern_period(int g) {
+  return g == 0 ? kWheelPeriod : kPatternPrimes[g][0] * kPatternPrimes[g][1] * kPatternPrimes[g][2];
+}
+constexpr uint32_t pattern_words(int g) { return (pattern_period(g) + 31) / 32 + kPatternPadWords; }
+// index (in the table 2, 3, 5, ...) of the first prime struck after presieving
+// with the wheel and `groups` groups: 8 primes up to 19, then 3 per group
+__host__ __device__ constexpr uint32_t first_struck_prime_index(int groups) { return 8u + 3u * (uint32_t)groups; }
+// largest presieved prime
+__host__ __device__ constexpr uint32_t last_presieved_prime(int groups) {
+  return groups == 0 ? 19u : kPatternPrimes[groups][2];
+}
+
+// Per-pattern layout in the pattern buffer: class 1 at off1, class 5 at off5.
+struct PatternDesc {
+  uint32_t period;
+  uint32_t off1, off5;
+  uint32_t pad_;
+  uint64_t magic;  // reciprocal64(period), for K0 mod period
+};
 
 // ---------------------------------------------------------------- arithmetic
 
@@ -109,6 +137,58 @@ __host__ __device__ __forceinline__ StartIndex table1_start(uint64_t B, uint64_t
   return s;
 }
 
+// Table 1 start indices for a tile with base B, start value M = B, and a
+// prime P with P^2 <= B and P < 2^31: Q = B - u with u = 1 + ((B - 1) mod P)
+// in [1, P], so the index near Q is I = floor(-u / 6) = -ceil(u / 6) and
+// q = Q mod 6 = (-u) mod 6; everything after the one 64-bit remainder is
+// 32-bit.  Same result as table1_start(B, B, P, m).
+__host__ __device__ __forceinline__ void table1_start_tile(uint64_t B, uint32_t P, uint64_t m, int32_t &id1,
+                                                  int32_t &id5) {
+  const uint64_t n = B - 1;
+  const uint64_t qq = mulhi64(n, m);
+  uint32_t r = (uint32_t)(n - qq * (uint64_t)P);
+  if (r >= P) r -= P;
+  const uint32_t u = r + 1;
+  const uint32_t cu = (u + 5) / 6;
+  const int32_t I = -(int32_t)cu;
+  const int32_t q = (int32_t)(6 * cu - u);
+  const int32_t R = (int32_t)(P / 6u);
+  int32_t a1, b1, a5, b5, Rp;
+  if (P % 6u == 1u) {
+    Rp = R;
+    a1 = q == 0 ? 1 : 7 - q;
+    b1 = q == 0 ? 0 : 1;
+    a5 = q == 5 ? 6 : 5 - q;
+    b5 = q == 5 ? 1 : 0;
+  } else {
+    Rp = R + 1;
+    a1 = q == 0 ? 5 : (q == 1 ? 6 : q - 1);
+    b1 = q <= 1 ? -1 : 0;
+    a5 = q + 1;
+    b5 = -1;
+  }
+  id1 = I + a1 * Rp + b1;
+  id5 = I + a5 * Rp + b5;
+}
+
+// Start indices of prime P in the tile with base B (M = B), as uint64 (every
+// start is >= 0): the 32-bit path when P^2 <= B and P < 2^31, else the
+// general one.  The kernels and the host entry sieve_table1_start use this.
+__host__ __device__ __forceinline__ void tile_starts(uint64_t B, uint32_t P, uint64_t m, uint64_t &k1,
+                                                     uint64_t &k5) {
+  const uint64_t P2 = (uint64_t)P * P;
+  if (P2 <= B && P < 0x80000000u) {
+    int32_t i1, i5;
+    table1_start_tile(B, P, m, i1, i5);
+    k1 = (uint64_t)(uint32_t)i1;
+    k5 = (uint64_t)(uint32_t)i5;
+  } else {
+    const StartIndex st = table1_start(B, B, P, m);
+    k1 = (uint64_t)st.id1;
+    k5 = (uint64_t)st.id5;
+  }
+}
+
 // ---------------------------------------------------------------- context
 
 struct DeviceTable {
@@ -134,7 +214,11 @@ struct sieve_ctx {
   uint32_t *d_primes = nullptr;
   uint64_t *d_magic = nullptr;
   std::vector<uint32_t> h_primes;  // host copy of the base table
-  uint32_t *d_pattern = nullptr;   // class-1 pattern, then class-5 pattern
+  // presieve patterns in the sliced layout, one set per tile width W = 2^logW
+  struct SlicedSet {
+    uint32_t *d = nullptr;
+    sieve::PatternDesc pd[sieve::kNumPatterns];
+  } sliced[32];
   sieve_options opt{};
   uint64_t launches = 0;
   // small device scratch: accumulators and status words
@@ -171,6 +255,10 @@ uint64_t isqrt_u64(uint64_t n);
 
 // cudaFuncAttributeMaxDynamicSharedMemorySize for the range kernels (range.cu)
 int range_set_smem_attributes(int bytes);
+
+// The presieve patterns in the sliced layout for tiles of W = 2^logW words per
+// class, built on first use (api.cu).
+int sliced_patterns(sieve_ctx *ctx, uint32_t logW, const uint32_t **ptr, PatternDesc *pd);
 
 // Range driver used by the public calls and by the base-table builder
 // (range.cu).  Output kinds for list mode: 4 (uint32) or 8 (uint64) bytes.

@@ -1,14 +1,27 @@
 // tile.cuh -- device routines for one segment ("tile") of the residue bitmaps.
 //
 // A CTA owns one tile at a time; its two bitmaps (class 1 and class 5, one bit
-// per candidate, bit j of word w = index 32 w + j) live in shared memory
-// (Sections 2.1-2.3: each worker sieves its own contiguous chunk in private
-// memory, so no two workers write the same address).
+// per candidate) live in shared memory (Sections 2.1-2.3: each worker sieves
+// its own contiguous chunk in private memory, so no two workers write the same
+// address).
+//
+// Bit-sliced layout: a tile of L = 32 W indices per class (W a power of two)
+// stores index k in word (k mod W), bit (k div W).  Shared-memory word w sits
+// in bank w mod 32 = k mod 32, so the 32 lanes of a warp that strike one prime
+// P at k, k + P, ..., k + 31 P always touch 32 different banks (P is odd): the
+// warp-cooperative strikes are free of bank conflicts for every P.  Row b of
+// the tile (bit b of every word) is the contiguous index run [b W, b W + W).
 #pragma once
 
 #include "sieve_internal.cuh"
 
 namespace sieve {
+
+// device copy of kPatternPrimes (one per translation unit)
+static __constant__ uint32_t c_pattern_primes[kNumPatterns][6] = {
+    {5, 7, 11, 13, 17, 19}, {23, 29, 31, 0, 0, 0},    {37, 41, 43, 0, 0, 0},
+    {47, 53, 59, 0, 0, 0},  {61, 67, 71, 0, 0, 0},    {73, 79, 83, 0, 0, 0},
+    {89, 97, 101, 0, 0, 0}, {103, 107, 109, 0, 0, 0}, {113, 127, 131, 0, 0, 0}};
 
 __device__ __forceinline__ uint32_t rotl32(uint32_t x, uint32_t s) { return __funnelshift_l(x, x, s); }
 
@@ -41,83 +54,142 @@ __device__ __forceinline__ uint32_t warp_count_le(const uint32_t *a, uint32_t n,
   return lo + __popc(__ballot_sync(kFullMask, le));
 }
 
-// Wheel presieve copy: word w of the tile receives the pattern bits
-// [o0 + 32 w, o0 + 32 w + 32) with o0 = K0 mod period.  A warp copies 32
-// consecutive words per step: one coalesced load per lane, the neighbour's
-// word by shuffle, a funnel shift for the bit phase.  Needs len <= period.
-template <int NWARPS>
-__device__ __forceinline__ void presieve_copy(uint32_t *s1, uint32_t *s5, uint32_t nwords,
-                                              uint64_t K0, const uint32_t *__restrict__ pat) {
-  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t o0 = (uint32_t)(K0 % kWheelPeriod);
-  for (uint32_t c = warp; c * 32 < nwords; c += NWARPS) {
-    uint32_t o = o0 + c * 1024u;
-    if (o >= kWheelPeriod) o -= kWheelPeriod;
-    const uint32_t wi = o >> 5, sh = o & 31;
-    const uint32_t w = c * 32 + lane;
-    uint32_t a1 = __ldg(pat + wi + lane);
-    uint32_t a5 = __ldg(pat + kPatternWords + wi + lane);
-    uint32_t b1 = __shfl_down_sync(kFullMask, a1, 1);
-    uint32_t b5 = __shfl_down_sync(kFullMask, a5, 1);
-    if (lane == 31) {
-      b1 = __ldg(pat + wi + 32);
-      b5 = __ldg(pat + kPatternWords + wi + 32);
+// Tile geometry shared by the phases.
+struct TileGeom {
+  uint32_t W;     // words per class (power of two, multiple of 32)
+  uint32_t logW;  // log2(W)
+  uint32_t len;   // indices in use (<= 32 W)
+};
+
+// Presieve copy.  For pattern g (period P_g), the sliced pattern T_g holds, at
+// word j, bit b = pattern bit (j + b W) mod P_g; so tile word w is
+// T_g[(K0 mod P_g) + w], a contiguous, coalesced copy.  Words of all patterns
+// in use are ANDed.
+template <int BLOCK>
+__device__ __forceinline__ void presieve_copy(uint32_t *s1, uint32_t *s5, const TileGeom &tg, uint64_t K0,
+                                              const uint32_t *__restrict__ sliced, const PatternDesc *pd,
+                                              int npat) {
+  uint32_t o[kNumPatterns];
+#pragma unroll
+  for (int g = 0; g < kNumPatterns; g++)
+    if (g < npat) o[g] = (uint32_t)(K0 - div_invariant(K0, pd[g].period, pd[g].magic) * pd[g].period);
+  for (uint32_t w = threadIdx.x; w < tg.W; w += BLOCK) {
+    uint32_t v1 = 0xFFFFFFFFu, v5 = 0xFFFFFFFFu;
+#pragma unroll
+    for (int g = 0; g < kNumPatterns; g++) {
+      if (g < npat) {
+        v1 &= __ldg(sliced + pd[g].off1 + o[g] + w);
+        v5 &= __ldg(sliced + pd[g].off5 + o[g] + w);
+      }
     }
-    if (w < nwords) {
-      s1[w] = __funnelshift_r(a1, b1, sh);
-      s5[w] = __funnelshift_r(a5, b5, sh);
-    }
+    s1[w] = v1;
+    s5[w] = v5;
   }
 }
 
-// Strike indices k = id, id + step, ... < len in bitmap s (Section 3: the
+// Strike indices k = k0, k0 + step, ... < len in bitmap s (Section 3: the
 // index advances by P, the value by 6P).  Clearing is an atomic AND in shared
-// memory because several lanes may clear bits of one word.
-__device__ __forceinline__ void strike(uint32_t *s, uint32_t k, uint32_t step, uint32_t len) {
-#pragma unroll 4
-  for (; k < len; k += step) atomicAnd(s + (k >> 5), rotl32(0xFFFFFFFEu, k));
+// memory because several lanes may clear bits of one word.  Four strikes per
+// loop trip and a predicated tail keep the branch count low.  step < 2^30.
+__device__ __forceinline__ void strike_one(uint32_t *s, uint32_t k, uint32_t wmask, uint32_t logW) {
+  atomicAnd(s + (k & wmask), rotl32(0xFFFFFFFEu, k >> logW));
+}
+
+__device__ __forceinline__ void strike(uint32_t *s, uint32_t k, uint32_t step, uint32_t len, uint32_t wmask,
+                                       uint32_t logW) {
+  if (step < len) {
+    const uint32_t s2 = 2 * step, s3 = 3 * step, s4 = 4 * step;
+    for (; k + s3 < len; k += s4) {
+      strike_one(s, k, wmask, logW);
+      strike_one(s, k + step, wmask, logW);
+      strike_one(s, k + s2, wmask, logW);
+      strike_one(s, k + s3, wmask, logW);
+    }
+    if (k + s2 < len) strike_one(s, k + s2, wmask, logW);
+    if (k + step < len) strike_one(s, k + step, wmask, logW);
+  }
+  if (k < len) strike_one(s, k, wmask, logW);
+}
+
+// Table 1 start indices of the warp-band primes [i_first, i_split) for the
+// tile with base B, one prime per thread, into shared memory (as 32-bit
+// indices; a start >= len means no hit, kept as len).
+template <int BLOCK>
+__device__ __forceinline__ void warp_band_starts(uint2 *starts, uint64_t B, uint32_t len,
+                                                 const uint32_t *__restrict__ primes,
+                                                 const uint64_t *__restrict__ magic, uint32_t i_first,
+                                                 uint32_t i_split) {
+  for (uint32_t i = i_first + threadIdx.x; i < i_split; i += BLOCK) {
+    uint64_t k1, k5;
+    tile_starts(B, __ldg(primes + i), __ldg(magic + i), k1, k5);
+    starts[i - i_first] = make_uint2(k1 < len ? (uint32_t)k1 : len, k5 < len ? (uint32_t)k5 : len);
+  }
 }
 
 // Strike every base prime with index in [i_first, np) into the tile whose
-// index 0 is value B and which holds len indices per class.  Primes with index
-// below i_split are struck by a whole warp (lane l takes hits l, l + 32, ...
-// of the prime); the rest by one lane each.
+// index 0 is value B.  Primes with index below i_split are struck by a whole
+// warp (lane l takes hits l, l + 32, ... of the prime; bank-conflict free in
+// the sliced layout) from the starts precomputed in shared memory, handed out
+// one at a time through a shared counter so that warps finish together; the
+// rest by one lane each.
 template <int BLOCK>
-__device__ __forceinline__ void strike_primes(uint32_t *s1, uint32_t *s5, uint64_t B, uint32_t len,
+__device__ __forceinline__ void strike_primes(uint32_t *s1, uint32_t *s5, uint64_t B, const TileGeom &tg,
                                               const uint32_t *__restrict__ primes,
-                                              const uint64_t *__restrict__ magic, uint32_t i_first,
-                                              uint32_t i_split, uint32_t np) {
-  constexpr int NWARPS = BLOCK / 32;
-  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+                                              const uint64_t *__restrict__ magic, const uint2 *starts,
+                                              uint32_t i_first, uint32_t i_split, uint32_t np, uint32_t *next) {
+  const uint32_t lane = threadIdx.x & 31;
   const uint32_t split = i_split < np ? i_split : np;
-  for (uint32_t i = i_first + warp; i < split; i += NWARPS) {
+  const uint32_t len = tg.len, wmask = tg.W - 1, logW = tg.logW;
+  for (;;) {
+    uint32_t i = 0;
+    if (lane == 0) i = atomicAdd(next, 1u);
+    i = __shfl_sync(kFullMask, i, 0);
+    if (i >= split) break;
     const uint32_t P = __ldg(primes + i);
-    const StartIndex st = table1_start(B, B, P, __ldg(magic + i));
-    const uint64_t k1 = (uint64_t)st.id1 + (uint64_t)lane * P;
-    const uint64_t k5 = (uint64_t)st.id5 + (uint64_t)lane * P;
-    if (k1 < len) strike(s1, (uint32_t)k1, 32u * P, len);
-    if (k5 < len) strike(s5, (uint32_t)k5, 32u * P, len);
+    const uint2 st = starts[i - i_first];
+    const uint32_t k1 = st.x + lane * P, k5 = st.y + lane * P;
+    if (k1 < len) strike(s1, k1, 32u * P, len, wmask, logW);
+    if (k5 < len) strike(s5, k5, 32u * P, len, wmask, logW);
   }
-  const uint32_t start = split > i_first ? split : i_first;
-  for (uint32_t i = start + threadIdx.x; i < np; i += BLOCK) {
-    const uint32_t P = __ldg(primes + i);
-    const StartIndex st = table1_start(B, B, P, __ldg(magic + i));
-    if ((uint64_t)st.id1 < len) strike(s1, (uint32_t)st.id1, P, len);
-    if ((uint64_t)st.id5 < len) strike(s5, (uint32_t)st.id5, P, len);
+  // one lane per prime; the next prime's table entries are loaded before the
+  // current prime is struck so that their latency overlaps the strikes
+  uint32_t i = (split > i_first ? split : i_first) + threadIdx.x;
+  uint32_t P = 0;
+  uint64_t m = 0;
+  if (i < np) {
+    P = __ldg(primes + i);
+    m = __ldg(magic + i);
+  }
+  while (i < np) {
+    const uint32_t in = i + BLOCK;
+    uint32_t Pn = 0;
+    uint64_t mn = 0;
+    if (in < np) {
+      Pn = __ldg(primes + in);
+      mn = __ldg(magic + in);
+    }
+    uint64_t k1, k5;
+    tile_starts(B, P, m, k1, k5);
+    if (k1 < len) strike(s1, (uint32_t)k1, P, len, wmask, logW);
+    if (k5 < len) strike(s5, (uint32_t)k5, P, len, wmask, logW);
+    i = in;
+    P = Pn;
+    m = mn;
   }
 }
 
 // ceil(a / 6) for signed a.
 __device__ __forceinline__ int64_t ceil_div6(int64_t a) { return -floor_div6(-a); }
 
-// Bits [lo_bit, hi_bit) of a word, bounds clamped to [0, 32].
-__device__ __forceinline__ uint32_t bit_range_mask(int64_t lo_bit, int64_t hi_bit) {
-  lo_bit = lo_bit < 0 ? 0 : (lo_bit > 32 ? 32 : lo_bit);
-  hi_bit = hi_bit < 0 ? 0 : (hi_bit > 32 ? 32 : hi_bit);
-  if (hi_bit <= lo_bit) return 0u;
-  uint32_t upto_hi = hi_bit == 32 ? 0xFFFFFFFFu : ((1u << hi_bit) - 1u);
-  uint32_t below_lo = lo_bit == 32 ? 0xFFFFFFFFu : ((1u << lo_bit) - 1u);
-  return upto_hi & ~below_lo;
+// Low n bits (n clamped to [0, 32]).
+__device__ __forceinline__ uint32_t low_bits(int64_t n) {
+  return n <= 0 ? 0u : (n >= 32 ? 0xFFFFFFFFu : ((1u << n) - 1u));
+}
+
+// Bits b of word w whose index w + b W lies below t: b < ceil((t - w) / W).
+__device__ __forceinline__ uint32_t below_mask(int64_t t, uint32_t w, uint32_t logW, uint32_t W) {
+  const int64_t d = t - (int64_t)w;
+  return d <= 0 ? 0u : low_bits((d + W - 1) >> logW);
 }
 
 // Valid indices of class r in a tile with base B: lo <= B + 6 k + r < hi.
@@ -140,39 +212,45 @@ __device__ __forceinline__ ValidRange valid_range(uint64_t lo, uint64_t hi, uint
 }
 
 // Fix-ups after striking (Section 2.1: the arrays hold candidates > 3):
-//   * tiles holding values below 24: clear the value 1, restore the wheel
-//     primes 5..19 (the presieve pattern removed them with their multiples);
+//   * tiles holding values up to the largest presieved prime: clear the value
+//     1 and restore the presieved primes themselves (their patterns removed
+//     them together with their multiples);
 //   * edge tiles: clear the bits outside [lo, hi) and past len.
 template <int BLOCK>
-__device__ __forceinline__ void fixup_tile(uint32_t *s1, uint32_t *s5, uint32_t len, uint32_t nwords,
-                                           uint64_t K0, const ValidRange &v) {
-  if (K0 < 4 && threadIdx.x == 0) {  // the tile holds values below 24
-    if (K0 == 0) s1[0] &= ~1u;       // 1 is not a prime
-    const uint32_t wheel[6] = {5, 7, 11, 13, 17, 19};
-    for (int q = 0; q < 6; q++) {
-      const uint32_t wv = wheel[q], r = wv % 6, k = wv / 6;
-      if (k >= K0 && k - K0 < len) (r == 1 ? s1 : s5)[(k - K0) >> 5] |= 1u << ((k - K0) & 31);
+__device__ __forceinline__ void fixup_tile(uint32_t *s1, uint32_t *s5, const TileGeom &tg, uint64_t K0,
+                                           const ValidRange &v, int npat) {
+  if (threadIdx.x == 0 && 6 * K0 <= 131) {
+    if (K0 == 0) s1[0] &= ~1u;  // 1 is not a prime (index 0: word 0, bit 0)
+    for (int g = 0; g < npat; g++) {
+      for (int q = 0; q < 6; q++) {
+        const uint32_t wv = c_pattern_primes[g][q];
+        if (wv == 0) continue;
+        const uint32_t r = wv % 6, k = wv / 6;
+        if (k >= K0 && k - K0 < tg.len) {
+          const uint32_t kk = (uint32_t)(k - K0);
+          (r == 1 ? s1 : s5)[kk & (tg.W - 1)] |= 1u << (kk >> tg.logW);
+        }
+      }
     }
   }
   __syncthreads();
-  const int64_t full = 32 * (int64_t)nwords;
+  const int64_t full = 32 * (int64_t)tg.W;
   if (v.kl1 > 0 || v.kl5 > 0 || v.kh1 < full || v.kh5 < full) {
-    for (uint32_t w = threadIdx.x; w < nwords; w += BLOCK) {
-      const int64_t base = 32 * (int64_t)w;
-      s1[w] &= bit_range_mask(v.kl1 - base, v.kh1 - base);
-      s5[w] &= bit_range_mask(v.kl5 - base, v.kh5 - base);
+    for (uint32_t w = threadIdx.x; w < tg.W; w += BLOCK) {
+      s1[w] &= below_mask(v.kh1, w, tg.logW, tg.W) & ~below_mask(v.kl1, w, tg.logW, tg.W);
+      s5[w] &= below_mask(v.kh5, w, tg.logW, tg.W) & ~below_mask(v.kl5, w, tg.logW, tg.W);
     }
   }
 }
 
-// Sum over the set bits j of x of j (x's bits are indices 32 w + j).
+// Sum over the set bits b of x of b.
 __device__ __forceinline__ uint32_t bit_index_sum(uint32_t x) {
   return __popc(x & 0xAAAAAAAAu) + (__popc(x & 0xCCCCCCCCu) << 1) + (__popc(x & 0xF0F0F0F0u) << 2) +
          (__popc(x & 0xFF00FF00u) << 3) + (__popc(x & 0xFFFF0000u) << 4);
 }
 
 // Interleave: bit 2j of the result is bit j of a, bit 2j+1 is bit j of b.
-// With a = class 1 and b = class 5 of one word, bit order = value order
+// With a = class 1 and b = class 5 of one index run, bit order = value order
 // (6k+1 < 6k+5 < 6(k+1)+1).
 __device__ __forceinline__ uint64_t spread_bits(uint32_t x) {
   uint64_t v = x;

@@ -109,12 +109,13 @@ def test_segment_counts_odd_widths(sv):
         assert np.array_equal(bins, obins), (lo, hi, w)
 
 
-@pytest.mark.parametrize("tile_bits", [1024, 4096, 32768, 3 << 17, 1 << 19])
+@pytest.mark.parametrize("tile_bits", [1024, 4096, 32768, 1 << 18, 1 << 19])
 @pytest.mark.parametrize("threads", [256, 512, 1024])
 def test_option_sweep(sv, tile_bits, threads):
     old = sv.options()
     try:
-        sv.set_options(tile_bits=tile_bits, block_threads=threads, group_hits=1 + (tile_bits % 7))
+        sv.set_options(tile_bits=tile_bits, block_threads=threads, group_hits=1 + (threads // 256),
+                       presieve_groups=(tile_bits.bit_length() + threads.bit_length()) % 9)
         for lo, hi in ((0, 3_000_000), (10**10 - 777, 10**10 + 4_000_000)):
             r = sv.range_count(lo, hi)
             assert (r.count, r.checksum) == oracle.count_range(lo, hi, base=_oracle_base(hi)), (lo, hi)
@@ -162,6 +163,8 @@ def test_errors(sv):
         sv.segment_counts(0, 10**6, 100)  # width below the minimum
     with pytest.raises(binding.SieveError):
         sv.set_options(tile_bits=1000)
+    with pytest.raises(binding.SieveError):
+        sv.set_options(tile_bits=3 << 10)  # not a power of two
     with pytest.raises(binding.SieveError):
         sv.set_options(tile_bits=1 << 20)  # 256 KB of bitmaps do not fit in shared memory
     r = sv.range_count(77, 77)

@@ -53,6 +53,22 @@ def test_large_values(scale):
             _check(B, M, P)
 
 
+def test_tile_path_m_equals_b():
+    """M == B is the kernels' per-tile case (32-bit path once P^2 <= B)."""
+    rng = np.random.default_rng(9)
+    primes = [p for p in range(5, 3000) if C.td_is_prime(p)] + [65521, 999983, 2147483647, 3037000493]
+    for P in primes:
+        for _ in range(10):
+            B = 6 * int(rng.integers(0, 10**17 // 6))
+            if max(B, P * P) - B < 2**62:
+                _check(B, B, P)
+        if P * P < 2**62:  # the entry's argument bound: max(M, P^2) - B < 2^62
+            _check(0, 0, P)
+        B = 6 * ((P * P) // 6)  # tile base just below P^2
+        _check(B, B, P)
+        _check(B + 6, B + 6, P)
+
+
 def test_square_start():
     """Section 2.4: a prime's strikes start at its square (5 -> 25 / 35, 7 -> 49 / 77)."""
     for P, s1, s5 in ((5, 25, 35), (7, 49, 77), (11, 121, 143), (13, 169, 221)):
