@@ -155,6 +155,40 @@ int sieve_segment_counts(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t seg_
                          uint64_t *counts, size_t ncounts, sieve_count_result *total,
                          unsigned flags);
 
+/* ------------------------------------------------------------- no allocation */
+
+/* Size of the fixed device scratch array used by sieve_range_list_noalloc. */
+#define SIEVE_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory when they need primes -- a process whose
+ * device memory belongs to another allocator, a latency-critical thread that
+ * must not pay for cudaMalloc / cudaFree (cudaFree synchronizes the device),
+ * a fixed memory budget.
+ *
+ * Same result as sieve_range(ctx, lo, hi, SIEVE_LIST, cnt, out, cap, n_out,
+ * SIEVE_OUT_DEVICE): the primes in [lo, hi), increasing, as uint64 in the
+ * caller's DEVICE buffer out[0..cap), *n_out = their number, *cnt (host, may
+ * be NULL) = count and checksum.  It allocates nothing: no cudaMalloc,
+ * cudaFree or allocating library routine.  It uses the context's base table
+ * and accumulators (made by sieve_create) and, as scratch for per-tile
+ * bitmaps, counts and offsets, one file-scope device array of
+ * SIEVE_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * exit.  The bitmaps take about one bit per 3 numbers, so a call covers a
+ * range of at most about 3.8e8 numbers; wider ranges return
+ * SIEVE_ERR_INVALID with a message giving the limit.  It does not presieve
+ * (the presieve patterns are allocated on demand by the other calls), so it
+ * is slower than sieve_range.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (on different streams or from different threads) race
+ * and give wrong results.  Errors: INVALID, RANGE, CAPACITY (nothing written
+ * when the list does not fit), CUDA. */
+int sieve_range_list_noalloc(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *out, size_t cap,
+                             size_t *n_out, sieve_count_result *cnt);
+
 /* ------------------------------------------------------------- table 1 */
 
 /* Host evaluation of the start-index routine the kernels run (Section 3,

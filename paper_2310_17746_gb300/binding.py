@@ -81,6 +81,7 @@ SIGNATURES = {
     "sieve_segment_counts": (_i, [_p, _u64, _u64, _u64, _p, _sz, _p, _u]),
     "sieve_table1_start": (_i, [_u64, _u64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int64),
                                 ctypes.POINTER(ctypes.c_int64)]),
+    "sieve_range_list_noalloc": (_i, [_p, _u64, _u64, _p, _sz, ctypes.POINTER(_sz), _p]),
 }
 
 
@@ -264,6 +265,18 @@ class Sieve:
         _check(self._lib.sieve_range(self._h, int(lo), int(hi), LIST, None, ptr, cap, ctypes.byref(nout), flags),
                "sieve_range")
         return int(nout.value)
+
+    def range_list_noalloc(self, lo: int, hi: int, out) -> tuple[int, CountAndSum]:
+        """Primes in [lo, hi) into the torch CUDA int64 tensor `out` through the
+        entry point that allocates nothing; returns (number, count/checksum)."""
+        if not _is_torch_cuda(out):
+            raise TypeError("out must be a torch CUDA tensor")
+        nout = _sz(0)
+        r = CountResult()
+        _check(self._lib.sieve_range_list_noalloc(self._h, int(lo), int(hi), out.data_ptr(), out.numel(),
+                                                  ctypes.byref(nout), ctypes.cast(ctypes.byref(r), _p)),
+               "sieve_range_list_noalloc")
+        return int(nout.value), CountAndSum(r.count, r.checksum)
 
     @staticmethod
     def nbins(lo: int, hi: int, seg_width: int) -> int:

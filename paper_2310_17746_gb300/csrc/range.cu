@@ -576,3 +576,149 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
 }
 
 }  // namespace sieve
+
+namespace sieve {
+
+// List-mode sieve of [lo, hi) into the device buffer `out` using caller-given
+// scratch and no allocation of any kind: no presieve patterns (every base
+// prime from 5 on is struck), the context's preallocated accumulators, and
+// `scratch` for the per-tile counts, offsets and bitmaps.  Used by the
+// entry point that allocates nothing (noalloc.cu).
+int run_range_list_into(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *out, size_t cap, size_t *n_out,
+                        sieve_count_result *cnt, void *scratch, size_t scratch_bytes) {
+  if (n_out) *n_out = 0;
+  if (cnt) {
+    cnt->count = 0;
+    cnt->checksum = 0;
+  }
+  if (lo > hi) {
+    set_error("lo (%llu) > hi (%llu)", (unsigned long long)lo, (unsigned long long)hi);
+    return SIEVE_ERR_INVALID;
+  }
+  if (hi > (1ull << 63)) {
+    set_error("hi must be <= 2^63");
+    return SIEVE_ERR_RANGE;
+  }
+  if (lo == hi) return SIEVE_OK;
+  const DeviceTable &table = ctx->table;
+  const uint64_t s = isqrt_u64(hi - 1);
+  if (s > table.limit) {
+    set_error("isqrt(hi - 1) = %llu exceeds the base table limit %llu", (unsigned long long)s,
+              (unsigned long long)table.limit);
+    return SIEVE_ERR_RANGE;
+  }
+  cudaStream_t st = ctx->stream;
+  const uint64_t k_begin = lo / 6;
+  const uint64_t k_end = (hi + 4) / 6;
+  const uint64_t span = k_end > k_begin ? k_end - k_begin : 0;
+  const int threads = (int)ctx->opt.block_threads;
+  uint32_t L = ctx->opt.tile_bits;
+  size_t smem = (size_t)L / 4;
+  int per_sm = 0;
+  int rc = dispatch_occupancy(threads, &per_sm, true, smem);
+  if (rc != SIEVE_OK) return rc;
+  if (per_sm < 1) {
+    set_error("tile of %u bits does not fit on an SM", L);
+    return SIEVE_ERR_INVALID;
+  }
+  if (ctx->opt.ctas_per_sm && (int)ctx->opt.ctas_per_sm < per_sm) per_sm = (int)ctx->opt.ctas_per_sm;
+  const uint64_t slots = (uint64_t)ctx->num_sms * (uint64_t)per_sm;
+  if (span > 0 && span < (uint64_t)L * slots) {
+    const uint64_t want = (span + slots - 1) / slots;
+    uint32_t lw = floor_pow2(want);
+    if (lw < want) lw *= 2;
+    if (lw < 1024) lw = 1024;
+    if (lw < L) L = lw;
+    smem = (size_t)L / 4;
+  }
+  const uint64_t ntiles64 = span ? (span + L - 1) / L : 0;
+  // scratch layout: [tile counts][offsets][bitmaps]
+  const size_t off_offsets = align_up((size_t)ntiles64 * sizeof(uint32_t), 256);
+  const size_t off_bitmap = align_up(off_offsets + ((size_t)ntiles64 + 1) * sizeof(uint64_t), 256);
+  const size_t need = off_bitmap + (size_t)ntiles64 * (L / 32) * sizeof(uint2);
+  if (ntiles64 > 0xFFFFFFF0ull || need > scratch_bytes) {
+    set_error("range [%llu, %llu) needs %zu bytes of scratch; the fixed scratch holds %zu "
+              "(roughly %llu numbers per call)",
+              (unsigned long long)lo, (unsigned long long)hi, need, scratch_bytes,
+              (unsigned long long)scratch_bytes * 22);
+    return SIEVE_ERR_INVALID;
+  }
+  const uint32_t ntiles = (uint32_t)ntiles64;
+  const int grid = (int)std::min<uint64_t>(ntiles ? ntiles : 1, slots);
+  const uint32_t np = host_prime_count_le_table(table, s);
+  const uint32_t i_first = 2;  // no presieve: strike from 5 on
+  const uint64_t gmax = L / (32ull * std::max<uint32_t>(1u, ctx->opt.group_hits));
+  uint32_t i_split = std::min(host_prime_count_le_table(table, gmax), np);
+  if (i_split < i_first) i_split = i_first;
+  smem += (size_t)(i_split - i_first) * sizeof(uint2);
+  if (smem > (size_t)ctx->smem_optin) {
+    set_error("tile of %u bits needs %zu bytes of shared memory", L, smem);
+    return SIEVE_ERR_INVALID;
+  }
+  char *scr = (char *)scratch;
+  RangeKernelParams p;
+  memset(&p, 0, sizeof(p));
+  p.lo = lo;
+  p.hi = hi;
+  p.k_begin = k_begin;
+  p.k_end = k_end;
+  p.L = L;
+  p.logW = log2u(L / 32);
+  p.ntiles = ntiles;
+  p.primes = table.primes;
+  p.magic = table.magic;
+  p.nprimes = np;
+  p.i_first = i_first;
+  p.i_split = i_split;
+  p.npat = 0;
+  p.sliced = nullptr;
+  p.count = ctx->d_acc;
+  p.checksum = ctx->d_acc + 1;
+  p.tile_counts = (uint32_t *)scr;
+  p.bitmap = (uint2 *)(scr + off_bitmap);
+  uint64_t *offsets = (uint64_t *)(scr + off_offsets);
+  SIEVE_CUDA_TRY(cudaMemsetAsync(ctx->d_acc, 0, 2 * sizeof(unsigned long long), st));
+  if (ntiles) {
+    rc = dispatch_launch(ctx, threads, p, true, grid, smem);
+    if (rc != SIEVE_OK) return rc;
+    scan_tile_counts_kernel<1024><<<1, 1024, 0, st>>>(p.tile_counts, offsets, ntiles);
+    ctx->launches++;
+    SIEVE_CUDA_TRY(cudaGetLastError());
+    SIEVE_CUDA_TRY(cudaMemcpyAsync(ctx->h_acc + 2, offsets + ntiles, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+  } else {
+    ctx->h_acc[2] = 0;
+  }
+  SIEVE_CUDA_TRY(cudaMemcpyAsync(ctx->h_acc, ctx->d_acc, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  SIEVE_CUDA_TRY(cudaStreamSynchronize(st));
+  const uint64_t total = ctx->h_acc[2];
+  if (n_out) *n_out = (size_t)total;
+  if (cnt) {
+    cnt->count = ctx->h_acc[0];
+    cnt->checksum = ctx->h_acc[1];
+  }
+  if (total > cap) {
+    set_error("output capacity %zu is below the %llu primes found", cap, (unsigned long long)total);
+    return SIEVE_ERR_CAPACITY;
+  }
+  if (total == 0) return SIEVE_OK;
+  CompactParams cp;
+  cp.lo = lo;
+  cp.hi = hi;
+  cp.k_begin = k_begin;
+  cp.k_end = k_end;
+  cp.L = L;
+  cp.logW = p.logW;
+  cp.ntiles = ntiles;
+  cp.bitmap = p.bitmap;
+  cp.offsets = offsets;
+  cp.out = out;
+  cp.cap = cap;
+  const int cgrid = (int)std::min<uint64_t>(ntiles, (uint64_t)ctx->num_sms * 4);
+  compact_kernel<256, uint64_t><<<cgrid, 256, 0, st>>>(cp);
+  ctx->launches++;
+  SIEVE_CUDA_TRY(cudaGetLastError());
+  SIEVE_CUDA_TRY(cudaStreamSynchronize(st));
+  return SIEVE_OK;
+}
+
+}  // namespace sieve
