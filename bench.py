@@ -100,7 +100,9 @@ def algorithmic_ops(lo: int, hi: int) -> dict:
 
 def source_hash() -> str:
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2310_17746_gb300", "csrc", "*"))):
+    # the files the count kernel is compiled from
+    for name in ("range.cu", "tile.cuh", "sieve_internal.cuh"):
+        f = os.path.join(ROOT, "paper_2310_17746_gb300", "csrc", name)
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -75,9 +75,10 @@ typedef struct {
   uint64_t checksum; /* sum of the primes found, modulo 2^64   */
 } sieve_count_result;
 
-/* Tunables of the segment kernels (the autotuner fills them; see
- * sieve_autotune).  Section 5 measures how the per-thread scratch array size
- * changes the run time; tile_bits is that knob here. */
+/* Tunables of the segment kernels (the autotuners fill them; see
+ * sieve_autotune_range / sieve_autotune_batch).  Section 5 measures how the
+ * per-thread scratch array size changes the run time; tile_bits is that knob
+ * here. */
 typedef struct {
   uint32_t tile_bits;      /* L: candidates per residue class per segment (multiple of 1024,
                               2 * L / 8 bytes of shared memory per CTA)                      */
@@ -88,7 +89,13 @@ typedef struct {
   uint32_t presieve_groups;  /* 0..8: besides the wheel {5..19}, how many groups of three
                               primes (23, 29, 31), (37, 41, 43), ... up to 131 are removed by
                               copying periodic patterns instead of striking                  */
-  uint32_t reserved[3];
+  uint32_t batch_tile_bits;  /* batch calls: largest tile (a query narrower than it gets a
+                              smaller power-of-two tile, at least 1024); 0 = tile_bits       */
+  uint32_t chunk_primes;   /* batch calls (>= 1024): a query whose base primes above the tile
+                              length, times its tiles, reach this number is "merged": those
+                              primes are applied by strip items of at most this many primes,
+                              each striking the query's bitmap in global memory             */
+  uint32_t reserved[1];
 } sieve_options;
 
 /* ---------------------------------------------------------------- context */
@@ -154,6 +161,63 @@ int sieve_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, int mode, sieve_count_
 int sieve_segment_counts(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t seg_width,
                          uint64_t *counts, size_t ncounts, sieve_count_result *total,
                          unsigned flags);
+
+/* ------------------------------------------------------------- batches */
+
+/* Many independent ranges in one call: query i is [lo[i], hi[i]) in mode
+ * mode[i] (SIEVE_COUNT or SIEVE_LIST).  Each query is the problem of Section
+ * 1.1 on its own range, sieved as in Sections 2-4; what the batch adds is the
+ * scheduling.  The queries are planned on the host into work items -- one
+ * per tile, sized to the query (a power of two of at least 1024 and at most
+ * sieve_options.batch_tile_bits indices per class), plus, for queries with
+ * many base primes above the tile length, "strips" that locate those primes
+ * once per query (Table 1) and clear their hits in a global bitmap with
+ * atomic ANDs -- and run by ONE persistent kernel launch that takes the items
+ * in decreasing estimated cost from an atomic counter.  The launch and its
+ * set-up / scan / compaction kernels are replayed as one CUDA graph.
+ *
+ * Inputs lo, hi, mode: HOST arrays of nq entries (the plan is built on the
+ * host).  Outputs, host or device memory per SIEVE_OUT_DEVICE:
+ *   cnt[nq]        count and checksum of every query (both modes);
+ *   offsets[nq+1]  list-mode primes of query i are values[offsets[i] ..
+ *                  offsets[i+1]) (count queries get an empty run);
+ *   values[cap]    the listed primes, uint64, each query's run increasing.
+ * *n_values (may be NULL) gets offsets[nq].  If it exceeds cap the call
+ * returns CAPACITY after filling cnt and offsets, writes nothing to values,
+ * and *n_values tells the size needed.  Per-query errors (lo > hi, mode not
+ * 0/1, hi beyond the base table) reject the whole batch (INVALID / RANGE,
+ * with the query index in the message).  Synchronous: returns after every
+ * output is complete.  The context keeps the batch buffers for the next call. */
+int sieve_range_batch(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, const uint8_t *mode, size_t nq,
+                      sieve_count_result *cnt, uint64_t *offsets, uint64_t *values, size_t cap,
+                      size_t *n_values, unsigned flags);
+
+/* The same contract answered the plain way: one sieve_range call (its own
+ * kernel launches and synchronisation) per query, in order.  It is the
+ * comparison point for sieve_range_batch.  On CAPACITY, *n_values is exact
+ * (the queries past the capacity are counted but not listed). */
+int sieve_range_each(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, const uint8_t *mode, size_t nq,
+                     sieve_count_result *cnt, uint64_t *offsets, uint64_t *values, size_t cap,
+                     size_t *n_values, unsigned flags);
+
+/* ------------------------------------------------------------- autotuning */
+
+/* Pick tunables by timing them, as Section 5 does for its per-thread array
+ * size.  Each candidate runs once untimed, then `reps` times under CUDA events
+ * on the context's stream; the one with the smallest median time becomes the
+ * context's options (returned in *best, time in *best_ms; either may be
+ * NULL).  Every candidate's results must equal the first candidate's, else
+ * the call fails with SIEVE_ERR_CUDA and the options are left unchanged.
+ *   sieve_autotune_batch: batch_tile_bits x block_threads x chunk_primes on
+ *     the given batch (host arrays, as sieve_range_batch); allocates and frees
+ *     its own device outputs.
+ *   sieve_autotune_range: tile_bits x block_threads x group_hits x
+ *     presieve_groups on the count of [lo, hi) (a sample of the ranges to
+ *     come; every candidate sieves it reps + 1 times). */
+int sieve_autotune_batch(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, const uint8_t *mode, size_t nq,
+                         int reps, sieve_options *best, double *best_ms);
+int sieve_autotune_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, int reps, sieve_options *best,
+                         double *best_ms);
 
 /* ------------------------------------------------------------- no allocation */
 

@@ -50,12 +50,14 @@ class CountResult(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("tile_bits", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
                 ("ctas_per_sm", ctypes.c_uint32), ("group_hits", ctypes.c_uint32),
-                ("presieve_groups", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+                ("presieve_groups", ctypes.c_uint32), ("batch_tile_bits", ctypes.c_uint32),
+                ("chunk_primes", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 1)]
 
     def as_dict(self) -> dict:
         return {"tile_bits": self.tile_bits, "block_threads": self.block_threads,
                 "ctas_per_sm": self.ctas_per_sm, "group_hits": self.group_hits,
-                "presieve_groups": self.presieve_groups}
+                "presieve_groups": self.presieve_groups, "batch_tile_bits": self.batch_tile_bits,
+                "chunk_primes": self.chunk_primes}
 
 
 _u64 = ctypes.c_uint64
@@ -82,6 +84,10 @@ SIGNATURES = {
     "sieve_table1_start": (_i, [_u64, _u64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int64),
                                 ctypes.POINTER(ctypes.c_int64)]),
     "sieve_range_list_noalloc": (_i, [_p, _u64, _u64, _p, _sz, ctypes.POINTER(_sz), _p]),
+    "sieve_range_batch": (_i, [_p, _p, _p, _p, _sz, _p, _p, _p, _sz, ctypes.POINTER(_sz), _u]),
+    "sieve_range_each": (_i, [_p, _p, _p, _p, _sz, _p, _p, _p, _sz, ctypes.POINTER(_sz), _u]),
+    "sieve_autotune_batch": (_i, [_p, _p, _p, _p, _sz, _i, ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_double)]),
+    "sieve_autotune_range": (_i, [_p, _u64, _u64, _i, ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_double)]),
 }
 
 
@@ -277,6 +283,76 @@ class Sieve:
                                                   ctypes.byref(nout), ctypes.cast(ctypes.byref(r), _p)),
                "sieve_range_list_noalloc")
         return int(nout.value), CountAndSum(r.count, r.checksum)
+
+    def _batch_call(self, fname, lo, hi, mode, cnt, offsets, values):
+        lo = np.ascontiguousarray(lo, dtype=np.uint64)
+        hi = np.ascontiguousarray(hi, dtype=np.uint64)
+        mode = np.ascontiguousarray(mode, dtype=np.uint8)
+        nq = lo.size
+        if hi.size != nq or mode.size != nq:
+            raise ValueError("lo, hi and mode must have the same length")
+        flags = 0
+        if _is_torch_cuda(cnt) or _is_torch_cuda(offsets) or _is_torch_cuda(values):
+            if not (_is_torch_cuda(cnt) and _is_torch_cuda(offsets) and (values is None or _is_torch_cuda(values))):
+                raise TypeError("device mode needs cnt, offsets (and values) as torch CUDA tensors")
+            flags = OUT_DEVICE
+        vptr = None if values is None else _ptr_and_flag(values)[0]
+        cap = 0 if values is None else (values.numel() if _is_torch_cuda(values) else values.size)
+        nout = _sz(0)
+        rc = getattr(self._lib, fname)(self._h, lo.ctypes.data, hi.ctypes.data, mode.ctypes.data, nq,
+                                       _ptr_and_flag(cnt)[0], _ptr_and_flag(offsets)[0], vptr, cap,
+                                       ctypes.byref(nout), flags)
+        return rc, int(nout.value)
+
+    def range_batch(self, lo, hi, mode, cnt=None, offsets=None, values=None, naive: bool = False):
+        """Many queries [lo[i], hi[i]) in one batched launch (mode[i]: COUNT or LIST).
+
+        Host mode (cnt/offsets/values None or numpy): returns (cnt, offsets,
+        values) as numpy uint64 arrays -- cnt[i] = (count, checksum), query
+        i's primes (list mode) at values[offsets[i]:offsets[i+1]].  Device
+        mode (torch CUDA tensors: cnt int64 (nq, 2), offsets int64 (nq + 1),
+        values int64): fills them and returns the number of listed primes.
+        naive=True answers with one range launch per query instead."""
+        fname = "sieve_range_each" if naive else "sieve_range_batch"
+        nq = int(np.asarray(lo).size)
+        if _is_torch_cuda(cnt):
+            rc, n = self._batch_call(fname, lo, hi, mode, cnt, offsets, values)
+            _check(rc, fname)
+            return n
+        cnt = np.zeros((nq, 2), dtype=np.uint64) if cnt is None else cnt
+        offsets = np.zeros(nq + 1, dtype=np.uint64) if offsets is None else offsets
+        if values is None:
+            rc, n = self._batch_call(fname, lo, hi, mode, cnt, offsets, None)
+            if rc == ERR_CAPACITY:
+                values = np.empty(max(n, 1), dtype=np.uint64)
+                rc, n = self._batch_call(fname, lo, hi, mode, cnt, offsets, values)
+            else:
+                values = np.empty(0, dtype=np.uint64)
+        else:
+            rc, n = self._batch_call(fname, lo, hi, mode, cnt, offsets, values)
+        _check(rc, fname)
+        return cnt, offsets, values[:n]
+
+    def autotune_batch(self, lo, hi, mode, reps: int = 2) -> tuple[dict, float]:
+        """Time the batch call over its tunables on these queries; the fastest
+        setting becomes the context's.  Returns (options, milliseconds)."""
+        lo = np.ascontiguousarray(lo, dtype=np.uint64)
+        hi = np.ascontiguousarray(hi, dtype=np.uint64)
+        mode = np.ascontiguousarray(mode, dtype=np.uint8)
+        o = Options()
+        ms = ctypes.c_double(0.0)
+        _check(self._lib.sieve_autotune_batch(self._h, lo.ctypes.data, hi.ctypes.data, mode.ctypes.data, lo.size,
+                                              int(reps), ctypes.byref(o), ctypes.byref(ms)), "sieve_autotune_batch")
+        return o.as_dict(), float(ms.value)
+
+    def autotune_range(self, lo: int, hi: int, reps: int = 2) -> tuple[dict, float]:
+        """Time the count kernel over its tunables on [lo, hi); the fastest
+        setting becomes the context's.  Returns (options, milliseconds)."""
+        o = Options()
+        ms = ctypes.c_double(0.0)
+        _check(self._lib.sieve_autotune_range(self._h, int(lo), int(hi), int(reps), ctypes.byref(o),
+                                              ctypes.byref(ms)), "sieve_autotune_range")
+        return o.as_dict(), float(ms.value)
 
     @staticmethod
     def nbins(lo: int, hi: int, seg_width: int) -> int:

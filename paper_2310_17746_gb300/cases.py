@@ -3,6 +3,7 @@
   python -m paper_2310_17746_gb300.cases count  LO HI [--seg W] [--reps R]
   python -m paper_2310_17746_gb300.cases list   LO HI [--reps R]
   python -m paper_2310_17746_gb300.cases primes32 N [--reps R]
+  python -m paper_2310_17746_gb300.cases batch  NQ [--seed S] [--count-only] [--reps R]
 
 Numbers accept Python expressions such as 10**10+1 or 2**30.  Options may
 set tile_bits / block_threads / group_hits.  Prints one line per repetition
@@ -24,7 +25,7 @@ def main(argv=None) -> int:
     from . import binding
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("kind", choices=["count", "list", "primes32"])
+    ap.add_argument("kind", choices=["count", "list", "primes32", "batch"])
     ap.add_argument("a", type=_num)
     ap.add_argument("b", type=_num, nargs="?")
     ap.add_argument("--seg", type=_num, default=0)
@@ -32,7 +33,14 @@ def main(argv=None) -> int:
     ap.add_argument("--tile-bits", type=_num, default=0)
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--group-hits", type=int, default=0)
+    ap.add_argument("--batch-tile-bits", type=_num, default=0)
+    ap.add_argument("--chunk-primes", type=_num, default=0)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--count-only", action="store_true")
+    ap.add_argument("--naive", action="store_true", help="batch: one range launch per query")
     args = ap.parse_args(argv)
+    if args.kind == "batch":
+        return _batch(args)
 
     hi = args.b if args.kind in ("count", "list") else args.a + 1
     lo = args.a if args.kind in ("count", "list") else 0
@@ -70,6 +78,40 @@ def main(argv=None) -> int:
         e.record(st)
         torch.cuda.synchronize()
         print(f"{args.kind} [{lo}, {hi}) rep {r}: {res} primes, {s.elapsed_time(e):.3f} ms", flush=True)
+    sv.close()
+    return 0
+
+
+def _batch(args) -> int:
+    """The batched-range workload (log-uniform lo in [1e6, 1e15], width in
+    [1e3, 1e8], half list mode) with device outputs."""
+    import numpy as np
+    import torch
+
+    from . import binding, workloads
+
+    q = workloads.batch_queries(n=args.a, seed=args.seed)
+    if args.count_only:
+        q.mode[:] = workloads.MODE_COUNT
+    nq = len(q)
+    sv = binding.Sieve(int(q.hi.max()) + 1)
+    opts = {k: v for k, v in (("batch_tile_bits", args.batch_tile_bits), ("block_threads", args.block_threads),
+                              ("chunk_primes", args.chunk_primes), ("group_hits", args.group_hits)) if v}
+    if opts:
+        sv.set_options(**opts)
+    cnt = torch.zeros((nq, 2), dtype=torch.int64, device="cuda")
+    off = torch.zeros(nq + 1, dtype=torch.int64, device="cuda")
+    cnt_h, _, _ = sv.range_batch(q.lo, q.hi, np.zeros(nq, np.uint8))
+    need = int(cnt_h[q.mode == workloads.MODE_LIST, 0].astype(np.int64).sum())
+    vals = torch.empty(max(need, 1), dtype=torch.int64, device="cuda")
+    st = torch.cuda.current_stream()
+    for r in range(args.reps):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(st)
+        n = sv.range_batch(q.lo, q.hi, q.mode, cnt=cnt, offsets=off, values=vals, naive=args.naive)
+        e.record(st)
+        torch.cuda.synchronize()
+        print(f"batch {nq} queries rep {r}: {n} listed, {s.elapsed_time(e):.3f} ms", flush=True)
     sv.close()
     return 0
 

@@ -176,6 +176,23 @@ int sliced_patterns(sieve_ctx *ctx, uint32_t logW, const uint32_t **ptr, Pattern
   return SIEVE_OK;
 }
 
+int ensure_pattern_set_dev(sieve_ctx *ctx, uint32_t logW) {
+  if (logW >= 32) {
+    set_error("tile width out of range");
+    return SIEVE_ERR_INVALID;
+  }
+  if (ctx->psets_ready & (1u << logW)) return SIEVE_OK;
+  if (!ctx->d_psets) SIEVE_CUDA_TRY(cudaMalloc(&ctx->d_psets, 32 * sizeof(PatternSetDev)));
+  PatternSetDev ps;
+  int rc = sliced_patterns(ctx, logW, &ps.d, ps.pd);
+  if (rc != SIEVE_OK) return rc;
+  // synchronous copy: ps lives on this stack frame
+  SIEVE_CUDA_TRY(cudaMemcpyAsync(ctx->d_psets + logW, &ps, sizeof(ps), cudaMemcpyHostToDevice, ctx->stream));
+  SIEVE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  ctx->psets_ready |= 1u << logW;
+  return SIEVE_OK;
+}
+
 }  // namespace sieve
 
 using namespace sieve;
@@ -184,6 +201,8 @@ using namespace sieve;
 
 static void free_ctx(sieve_ctx *c) {
   if (!c) return;
+  destroy_batch_runner(c->batch);
+  cudaFree(c->d_psets);
   cudaFree(c->d_primes);
   cudaFree(c->d_magic);
   for (auto &ss : c->sliced) cudaFree(ss.d);
@@ -202,6 +221,8 @@ static sieve_options default_options() {
   o.ctas_per_sm = 0;
   o.group_hits = 4;
   o.presieve_groups = 2;
+  o.batch_tile_bits = 1u << 18;
+  o.chunk_primes = 1u << 15;
   return o;
 }
 
@@ -225,6 +246,15 @@ static int validate_options(const sieve_ctx *c, const sieve_options &o) {
   }
   if (o.group_hits == 0 || o.group_hits > 1024) {
     set_error("group_hits must be in [1, 1024]");
+    return SIEVE_ERR_INVALID;
+  }
+  if (o.batch_tile_bits && (o.batch_tile_bits < 1024 || (o.batch_tile_bits & (o.batch_tile_bits - 1)) ||
+                            o.batch_tile_bits > (1u << 19) || (int)(o.batch_tile_bits / 4) > c->smem_optin)) {
+    set_error("batch_tile_bits must be 0 or a power of two in [1024, 2^19] that fits in shared memory");
+    return SIEVE_ERR_INVALID;
+  }
+  if (o.chunk_primes < 1024) {
+    set_error("chunk_primes must be >= 1024");
     return SIEVE_ERR_INVALID;
   }
   if (o.presieve_groups > (uint32_t)kMaxPresieveGroups) {

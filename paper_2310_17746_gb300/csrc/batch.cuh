@@ -1,0 +1,89 @@
+// batch.cuh -- many [lo, hi) queries sieved by one persistent launch.
+//
+// A batch is planned on the host into work items, uploaded as one block (the
+// "plan"), and run as a fixed sequence of kernels captured in a CUDA graph:
+//   init -> sieve (persistent, items taken from an atomic counter in cost
+//   order) -> finish (merged tiles) -> scan (list offsets) -> compact.
+//
+// Work items (Sections 2.2-2.3: independent workers on contiguous chunks;
+// Section 3: per-prime start indices):
+//   * tile item: one tile of one query, sieved in shared memory as in the
+//     single-range kernel, for the base primes [i0, i1).  A query's tile is
+//     sized to the query (a power of two >= 1024 indices per class, at most
+//     the batch tile size), so narrow queries use small tiles.
+//   * strip item: base primes [i0, i1) that exceed the tile length, applied to
+//     a whole query at once: each prime's first index comes from one Table 1
+//     evaluation for the query, then every later hit (index + P) is cleared
+//     with an atomic AND in the query's bitmap in global memory.  This is the
+//     work a bucket sieve saves for primes larger than a segment: a prime is
+//     located once per query instead of once per tile, and a tile pays only
+//     for the hits that land in it.
+// Queries with strips are "merged": their tiles live in global memory (all
+// ones after init); tile items AND their shared-memory result into it, strips
+// strike it directly, and the finish kernel counts / emits each merged tile
+// after the sieve kernel has ended (a kernel boundary orders them, so no
+// kernel waits on another CTA).
+#pragma once
+
+#include "sieve_internal.cuh"
+
+namespace sieve {
+
+constexpr uint32_t kStrip = 0xFFFFFFFFu;  // BatchItem::t of a strip item
+
+struct BatchQuery {
+  uint64_t lo, hi;          // [lo, hi)
+  uint64_t k_begin, k_end;  // class indices; tile t covers [k_begin + t L, ...) up to k_end
+  uint64_t bitmap_off;      // list mode: uint2 offset of tile 0's bitmap in the list scratch
+  uint64_t slot_base;       // merged: u32 offset of tile 0 in the merge bitmaps (2 W words per tile)
+  uint64_t out_base;        // fixed-output mode: element offset of this query's list
+  uint64_t out_cap;         // fixed-output mode: elements reserved for it
+  uint32_t logL, ntiles;    // tile length L = 2^logL indices per class
+  uint32_t np;              // primes[0..np) cover isqrt(hi - 1)
+  uint32_t i_split;         // primes below this index are struck by whole warps
+  uint32_t ltile0;          // list tiles of the queries before this one
+  uint32_t flags;           // bit 0: list mode, bit 1: merged
+};
+
+constexpr uint32_t kQueryList = 1u, kQueryMerged = 2u;
+
+struct BatchItem {
+  uint32_t q, t;    // query; tile within it, or kStrip
+  uint32_t i0, i1;  // base-prime indices [i0, i1)
+};
+
+// Start of the uploaded plan.  Section offsets are bytes from the plan start.
+struct BatchHeader {
+  uint32_t nq, nitems, nmerged, nltiles;
+  uint64_t slot_words;   // u32 words of merge bitmaps (all ones after init)
+  uint64_t off_queries, off_items, off_mtiles, off_ltiles, off_ltile0;
+  uint64_t *values;      // list output (device memory)
+  uint64_t cap;          // CSR mode: capacity of values
+  uint32_t fixed_out;    // 0: CSR (query q at offsets[q]); 1: query q at out_base
+  uint32_t npat;         // presieve patterns in use
+};
+
+// Device-written state of one batch.
+struct BatchState {
+  uint32_t next_item;
+  uint32_t status;  // bit 0: CSR capacity exceeded; bit 1: a query exceeded its out_cap
+};
+
+// Device buffers of a batch arena (kernel parameters; fixed for a graph).
+struct BatchArena {
+  const void *plan;
+  BatchState *state;
+  unsigned long long *acc;  // 2 per query: count, checksum
+  uint32_t *slot_bm;        // merge bitmaps
+  uint32_t *tile_counts;    // per list tile
+  uint64_t *tile_off;       // per list tile + 1
+  uint64_t *offsets;        // per query + 1
+  uint2 *list_bm;           // list tiles' bitmaps
+  const uint32_t *primes;
+  const uint64_t *magic;
+  const PatternSetDev *psets;  // indexed by log2(W)
+  uint32_t Wmax;               // words per class of the largest tile
+  uint32_t band_max;           // warp-band start slots in shared memory
+};
+
+}  // namespace sieve

@@ -56,6 +56,12 @@ struct PatternDesc {
   uint64_t magic;  // reciprocal64(period), for K0 mod period
 };
 
+// A set of presieve patterns for one tile width, as the batch kernels see it.
+struct PatternSetDev {
+  const uint32_t *d;
+  PatternDesc pd[kNumPatterns];
+};
+
 // ---------------------------------------------------------------- arithmetic
 
 __host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
@@ -141,19 +147,20 @@ __host__ __device__ __forceinline__ StartIndex table1_start(uint64_t B, uint64_t
 // prime P with P^2 <= B and P < 2^31: Q = B - u with u = 1 + ((B - 1) mod P)
 // in [1, P], so the index near Q is I = floor(-u / 6) = -ceil(u / 6) and
 // q = Q mod 6 = (-u) mod 6; everything after the one 64-bit remainder is
-// 32-bit.  Same result as table1_start(B, B, P, m).
-__host__ __device__ __forceinline__ void table1_start_tile(uint64_t B, uint32_t P, uint64_t m, int32_t &id1,
-                                                  int32_t &id5) {
+// 32-bit.  The sum I + a R' + b is formed modulo 2^32 (unsigned, so that the
+// wrap is defined); the start itself is in [0, 2^32) for P < 2^31, so the
+// result is exact.  Same result as table1_start(B, B, P, m).
+__host__ __device__ __forceinline__ void table1_start_tile(uint64_t B, uint32_t P, uint64_t m, uint32_t &id1,
+                                                           uint32_t &id5) {
   const uint64_t n = B - 1;
   const uint64_t qq = mulhi64(n, m);
   uint32_t r = (uint32_t)(n - qq * (uint64_t)P);
   if (r >= P) r -= P;
   const uint32_t u = r + 1;
   const uint32_t cu = (u + 5) / 6;
-  const int32_t I = -(int32_t)cu;
-  const int32_t q = (int32_t)(6 * cu - u);
-  const int32_t R = (int32_t)(P / 6u);
-  int32_t a1, b1, a5, b5, Rp;
+  const uint32_t q = 6 * cu - u;
+  const uint32_t R = P / 6u;
+  uint32_t a1, b1, a5, b5, Rp;
   if (P % 6u == 1u) {
     Rp = R;
     a1 = q == 0 ? 1 : 7 - q;
@@ -163,12 +170,12 @@ __host__ __device__ __forceinline__ void table1_start_tile(uint64_t B, uint32_t 
   } else {
     Rp = R + 1;
     a1 = q == 0 ? 5 : (q == 1 ? 6 : q - 1);
-    b1 = q <= 1 ? -1 : 0;
+    b1 = q <= 1 ? 0xFFFFFFFFu : 0;  // -1
     a5 = q + 1;
-    b5 = -1;
+    b5 = 0xFFFFFFFFu;               // -1
   }
-  id1 = I + a1 * Rp + b1;
-  id5 = I + a5 * Rp + b5;
+  id1 = a1 * Rp + b1 - cu;
+  id5 = a5 * Rp + b5 - cu;
 }
 
 // Start indices of prime P in the tile with base B (M = B), as uint64 (every
@@ -178,10 +185,10 @@ __host__ __device__ __forceinline__ void tile_starts(uint64_t B, uint32_t P, uin
                                                      uint64_t &k5) {
   const uint64_t P2 = (uint64_t)P * P;
   if (P2 <= B && P < 0x80000000u) {
-    int32_t i1, i5;
+    uint32_t i1, i5;
     table1_start_tile(B, P, m, i1, i5);
-    k1 = (uint64_t)(uint32_t)i1;
-    k5 = (uint64_t)(uint32_t)i5;
+    k1 = i1;
+    k5 = i5;
   } else {
     const StartIndex st = table1_start(B, B, P, m);
     k1 = (uint64_t)st.id1;
@@ -198,6 +205,8 @@ struct DeviceTable {
   uint32_t nprimes = 0;
   uint64_t limit = 0;
 };
+
+struct BatchRunner;  // batch.cu
 
 // Number of table primes <= s (host binary search).
 uint32_t host_prime_count_le_table(const DeviceTable &t, uint64_t s);
@@ -221,6 +230,12 @@ struct sieve_ctx {
   } sliced[32];
   sieve_options opt{};
   uint64_t launches = 0;
+  // device copy of the pattern sets, indexed by log2(W); entry i is valid
+  // when bit i of psets_ready is set
+  sieve::PatternSetDev *d_psets = nullptr;
+  uint32_t psets_ready = 0;
+  // batch runner of the synchronous batch call (batch.cu)
+  sieve::BatchRunner *batch = nullptr;
   // small device scratch: accumulators and status words
   unsigned long long *d_acc = nullptr;
   size_t acc_words = 0;
@@ -259,6 +274,11 @@ int range_set_smem_attributes(int bytes);
 // The presieve patterns in the sliced layout for tiles of W = 2^logW words per
 // class, built on first use (api.cu).
 int sliced_patterns(sieve_ctx *ctx, uint32_t logW, const uint32_t **ptr, PatternDesc *pd);
+// Make sure the device table entry for log2(W) = logW is filled (api.cu).
+int ensure_pattern_set_dev(sieve_ctx *ctx, uint32_t logW);
+
+// batch runner lifetime (batch.cu)
+void destroy_batch_runner(BatchRunner *r);
 
 // Range driver used by the public calls and by the base-table builder
 // (range.cu).  Output kinds for list mode: 4 (uint32) or 8 (uint64) bytes.

@@ -295,4 +295,55 @@ __device__ __forceinline__ void block_sum3(uint64_t &a, uint64_t &b, uint64_t &c
   }
 }
 
+// Write the survivors of one tile, in value order, to out[off, ...).  The
+// tile's bitmap bm holds W = 2^logW (class-1 word, class-5 word) pairs in the
+// sliced layout.  Row b of the tile is the index run [b W, b W + W); a unit
+// (b, c) is the 32 indices b W + 32 c + j, j = 0..31, and units in row-major
+// order are in value order.  A warp reads the 32 words of chunk c and
+// extracts row b of each class with one ballot (the ballot transposes the
+// bits), interleaves the two classes in value order and lane j writes the
+// values of bits 2j and 2j+1.  Each warp owns a contiguous run of units; a
+// first pass counts them and a block scan (in warp_base, NWARPS entries)
+// places the warps.  Bits outside the valid range must already be clear.
+template <int BLOCK, typename OutT>
+__device__ __forceinline__ void compact_tile(const uint2 *__restrict__ bm, uint32_t logW, uint32_t units,
+                                             uint32_t chunk_bits, uint64_t K0, uint64_t off, OutT *out,
+                                             uint64_t *warp_base) {
+  constexpr int NWARPS = BLOCK / 32;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t per_warp = (units + NWARPS - 1) / NWARPS;
+  const uint32_t u_begin = min(warp * per_warp, units);
+  const uint32_t u_end = min(u_begin + per_warp, units);
+  uint32_t c = 0;
+  for (uint32_t u = u_begin; u < u_end; u++) {
+    const uint32_t b = u >> chunk_bits, w = ((u & ((1u << chunk_bits) - 1)) << 5) + lane;
+    const uint2 x = bm[w];
+    c += __popc(__ballot_sync(kFullMask, (x.x >> b) & 1u)) + __popc(__ballot_sync(kFullMask, (x.y >> b) & 1u));
+  }
+  if (lane == 0) warp_base[warp] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t run = off;
+    for (int i = 0; i < NWARPS; i++) {
+      const uint64_t ci = warp_base[i];
+      warp_base[i] = run;
+      run += ci;
+    }
+  }
+  __syncthreads();
+  uint64_t base = warp_base[warp];
+  for (uint32_t u = u_begin; u < u_end; u++) {
+    const uint32_t b = u >> chunk_bits, c0 = (u & ((1u << chunk_bits) - 1)) << 5;
+    const uint2 x = bm[c0 + lane];
+    const uint32_t m1 = __ballot_sync(kFullMask, (x.x >> b) & 1u);
+    const uint32_t m5 = __ballot_sync(kFullMask, (x.y >> b) & 1u);
+    const uint64_t z = interleave_classes(m1, m5);
+    const uint64_t vb = 6 * (K0 + ((uint64_t)b << logW) + c0 + lane);
+    const uint32_t q1 = 2 * lane, q5 = 2 * lane + 1;
+    if ((z >> q1) & 1ull) out[base + __popcll(z & ((1ull << q1) - 1))] = (OutT)(vb + 1);
+    if ((z >> q5) & 1ull) out[base + __popcll(z & ((1ull << q5) - 1))] = (OutT)(vb + 5);
+    base += __popcll(z);
+  }
+}
+
 }  // namespace sieve
