@@ -44,6 +44,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-queries leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
@@ -250,6 +252,180 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- GPU arm
 
+# ---------------------------------------------------------------- batch and serving legs
+
+def batch_leg(steps: int, warmup: int) -> dict:
+    """Batched range queries/s: the 4096-query workload (seed 0: lo log-uniform
+    in [1e6, 1e15], width in [1e3, 1e8], half list mode) in one batched call,
+    after the autotuner picked its tunables; against one range launch per query
+    on the same GPU; and end to end with host output buffers."""
+    import numpy as np
+    import torch
+
+    from paper_2310_17746_gb300 import binding, workloads
+
+    q = workloads.batch_queries()
+    nq = len(q)
+    sv = binding.Sieve(int(q.hi.max()) + 1)
+    t0 = time.perf_counter()
+    tuned, tuned_ms = sv.autotune_batch(q.lo, q.hi, q.mode, reps=1)
+    tune_s = time.perf_counter() - t0
+    dev = torch.device("cuda")
+    cnt_h, _, _ = sv.range_batch(q.lo, q.hi, np.zeros(nq, np.uint8))
+    list_mask = q.mode == workloads.MODE_LIST
+    need = int(cnt_h[list_mask, 0].astype(np.int64).sum())
+    c = torch.zeros((nq, 2), dtype=torch.int64, device=dev)
+    o = torch.zeros(nq + 1, dtype=torch.int64, device=dev)
+    v = torch.empty(max(need, 1), dtype=torch.int64, device=dev)
+    st = torch.cuda.current_stream(dev)
+    launches0 = sv.launch_count()
+    for _ in range(max(warmup, 3)):
+        sv.range_batch(q.lo, q.hi, q.mode, cnt=c, offsets=o, values=v)
+    torch.cuda.synchronize()
+    ts = []
+    launches1 = sv.launch_count()
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        sv.range_batch(q.lo, q.hi, q.mode, cnt=c, offsets=o, values=v)
+        b.record(st)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b) / 1e3)
+    per_call_launches = (sv.launch_count() - launches1) / steps
+    got = c.cpu().numpy().astype(np.uint64)
+    assert np.array_equal(got, cnt_h), "batched list run disagrees with the count-only run"
+    t_dev = statistics.mean(ts)
+    # one range launch per query (same outputs, device memory)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sv.range_batch(q.lo, q.hi, q.mode, cnt=c, offsets=o, values=v, naive=True)
+    torch.cuda.synchronize()
+    t_naive = time.perf_counter() - t0
+    # end to end with host buffers (pinned, so the copies run at full speed)
+    hc = torch.zeros((nq, 2), dtype=torch.int64).pin_memory().numpy()
+    ho = torch.zeros(nq + 1, dtype=torch.int64).pin_memory().numpy()
+    hv = torch.empty(max(need, 1), dtype=torch.int64).pin_memory().numpy()
+    sv.range_batch(q.lo, q.hi, q.mode, cnt=hc, offsets=ho, values=hv)
+    te = []
+    for _ in range(max(1, min(steps, 3))):
+        t0 = time.perf_counter()
+        sv.range_batch(q.lo, q.hi, q.mode, cnt=hc, offsets=ho, values=hv)
+        te.append(time.perf_counter() - t0)
+    sv.close()
+    return {
+        "metric": "batched range queries/s", "value": nq / t_dev, "unit": "queries/s",
+        "ms_per_batch": 1e3 * t_dev, "queries": nq, "list_primes": need,
+        "workload": "4096 queries, seed 0: lo = floor(10^U(6,15)), width = floor(10^U(3,8)), half list mode "
+                    "(uint64 primes, CSR), base primes <= 3.2e7 on the device",
+        "naive_one_launch_per_query": {"value": nq / t_naive, "unit": "queries/s", "ms": 1e3 * t_naive},
+        "speedup_vs_naive": t_naive / t_dev,
+        "e2e": {"value": nq / statistics.mean(te), "unit": "queries/s",
+                "h2d_bytes_per_step": int(nq * 17), "d2h_bytes_per_step": int(nq * 16 + (nq + 1) * 8 + need * 8)},
+        "list_write_gbs": need * 8 / t_dev / 1e9,
+        "autotuned": {k: tuned[k] for k in ("batch_tile_bits", "block_threads", "chunk_primes")},
+        "autotune_s": tune_s, "kernels_per_call": per_call_launches,
+        "l2": "outputs (6 GB of primes) exceed L2; no flush",
+    }
+
+
+def serving_leg(rates=(1000, 3000, 10000, 30000, 100000), seconds: float = 1.0, max_n: int = 40000) -> dict:
+    """Open-loop Poisson request streams (seed 1: lo log-uniform in [1e6, 1e18],
+    width in [1e3, 1e9], 20% list mode) against the continuous-batching server;
+    latency = submit to result ready on the server.  Results are collected into
+    device memory.  Compared with one range launch per request in arrival order
+    at the lowest rates."""
+    import threading as th
+
+    import numpy as np
+    import torch
+
+    from paper_2310_17746_gb300 import binding, workloads
+
+    dev = torch.device("cuda")
+    sv = binding.Sieve(10**18 + 10**9 + 1)  # base primes <= 1e9 on the device
+    scratch = torch.empty(1 << 27, dtype=torch.int64, device=dev)  # 1 GiB landing zone for lists
+    out = {"workload": "Poisson arrivals, seed 1: lo = floor(10^U(6,18)), width = floor(10^U(3,9)), "
+                       "list with probability 0.2; base primes <= 1e9 on the device", "rates": []}
+    srv = binding.Server(sv, pool_bytes=32 << 30)
+    def drain(expected: int, timeout_s: float) -> int:
+        """Collect finished requests until `expected` were collected."""
+        got, t_end = 0, time.perf_counter() + timeout_s
+        while got < expected and time.perf_counter() < t_end:
+            rid = srv.next_done(timeout_us=2000)
+            if rid is not None:
+                got += srv.poll(rid, out=scratch) is not None
+        return got
+
+    # warm-up: every tile width and the strip path
+    warm = workloads.serving_arrivals(1000.0, 200, seed=99)
+    ids = [srv.submit(int(a), int(b), int(m)) for a, b, m in zip(warm.queries.lo, warm.queries.hi, warm.queries.mode)]
+    drain(len(ids), 120.0)
+    srv.stats(reset=True)
+    for rate in rates:
+        n = int(min(max_n, rate * seconds))
+        arr = workloads.serving_arrivals(float(rate), n, seed=1)
+        lo, hi, mode = arr.queries.lo.tolist(), arr.queries.hi.tolist(), arr.queries.mode.tolist()
+        t_arr = arr.t_arrive.tolist()
+        admitted = [0]
+        rejected = [0]
+        done_flag = [False]
+        collected = [0]
+
+        def collector():
+            while not done_flag[0] or collected[0] < admitted[0]:
+                rid = srv.next_done(timeout_us=2000)
+                if rid is not None:
+                    collected[0] += srv.poll(rid, out=scratch) is not None
+                elif done_flag[0] and time.perf_counter() - t0 > t_limit:
+                    return
+
+        t_limit = seconds * 20 + 30
+        t0 = time.perf_counter()
+        col = th.Thread(target=collector)
+        col.start()
+        for i in range(n):
+            while time.perf_counter() - t0 < t_arr[i]:
+                pass
+            if srv.try_submit(lo[i], hi[i], mode[i]) is None:
+                rejected[0] += 1
+            else:
+                admitted[0] += 1
+        t_sub = time.perf_counter() - t0
+        done_flag[0] = True
+        col.join()
+        t_end = time.perf_counter() - t0
+        st = srv.stats(reset=True)
+        out["rates"].append({
+            "offered_per_s": rate, "requests": n, "admitted": admitted[0], "rejected_busy": rejected[0],
+            "completed": collected[0], "queries_per_s": collected[0] / t_end, "submit_s": t_sub, "p50_us": st["p50_us"],
+            "p99_us": st["p99_us"], "mean_us": st["mean_us"], "max_us": st["max_us"],
+            "batches": st["batches"], "mean_batch": st["mean_batch"], "overlapped_batches": st["overlapped_batches"]})
+    srv.stop()
+    # one range launch per request, in arrival order, at the lowest rates
+    naive = []
+    for rate in rates[:2]:
+        n = int(min(2000, rate * seconds))
+        arr = workloads.serving_arrivals(float(rate), n, seed=1)
+        lat = []
+        t0 = time.perf_counter()
+        for i in range(n):
+            while time.perf_counter() - t0 < arr.t_arrive[i]:
+                pass
+            a, b, m = int(arr.queries.lo[i]), int(arr.queries.hi[i]), int(arr.queries.mode[i])
+            if m == workloads.MODE_LIST:
+                sv.range_list(a, b, out=scratch)
+            else:
+                sv.range_count(a, b)
+            lat.append(time.perf_counter() - t0 - arr.t_arrive[i])
+        t_end = time.perf_counter() - t0
+        lat.sort()
+        naive.append({"offered_per_s": rate, "requests": n, "queries_per_s": n / t_end,
+                      "p50_us": 1e6 * lat[len(lat) // 2], "p99_us": 1e6 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]})
+    out["naive_one_launch_per_query"] = naive
+    sv.close()
+    return out
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -345,6 +521,12 @@ def run_gpu(args):
     opts = sv.options()
     traffic = profiled_traffic("range_tiles_count_1e12.json")
 
+    batch = serving = None
+    if world == 1 and not args.no_batch:
+        batch = batch_leg(args.steps, args.warmup)
+    if world == 1 and not args.no_serving:
+        serving = serving_leg()
+
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         w, spent, times, cores = oracle_sample(args.cpu_seconds)
@@ -373,6 +555,8 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16,
                 "d2h_bytes_per_step": 8 * nb + 16},
         "gpu_launches": launches,
+        "batch": batch,
+        "serving": serving,
         "clocks": clk,
         "wall_s_timed": wall,
     }

@@ -219,6 +219,65 @@ int sieve_autotune_batch(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi,
 int sieve_autotune_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, int reps, sieve_options *best,
                          double *best_ms);
 
+/* ------------------------------------------------------------- serving */
+
+/* A request loop with continuous batching on top of sieve_range_batch's
+ * machinery.  Clients submit [lo, hi) queries from any thread; a server
+ * thread forms batches from the admitted requests and runs each as one
+ * batched launch on one of two streams, so that a batch formed while another
+ * is on the GPU overlaps it (the paper's per-chunk workers, Sections 2.2-2.3,
+ * fed from a queue instead of a fixed split).  Results stay on the device
+ * until collected.
+ *
+ * Admission is by device memory: a list-mode request reserves, at submit, room
+ * for the largest possible answer (min(2 ceil(w/6) + 2, 2 w / ln w + 64)
+ * primes for width w; the second is the Montgomery-Vaughan bound with slack)
+ * in a device pool of pool_bytes, and returns it when collected.  A full pool
+ * or queue makes submit return SIEVE_ERR_BUSY (nothing is queued; retry
+ * later).  While a server runs on a context, make no other call on that
+ * context. */
+typedef struct {
+  size_t pool_bytes;           /* device pool for list results awaiting collection        */
+  size_t max_batch;            /* requests per batch (0: 4096)                             */
+  size_t max_queue;            /* admitted requests waiting for a batch (0: 65536)         */
+  size_t batch_scratch_bytes;  /* scratch a batch may plan for; a request above it runs
+                                  alone (0: 1 GiB)                                         */
+} sieve_server_config;
+
+typedef struct {
+  uint64_t completed;           /* requests answered since start or the last reset        */
+  uint64_t rejected;            /* submits refused with SIEVE_ERR_BUSY                    */
+  uint64_t batches;             /* batches launched                                       */
+  uint64_t overlapped_batches;  /* batches launched while the other stream was busy       */
+  uint64_t queued;              /* requests admitted and waiting now                      */
+  uint64_t pool_used_bytes;     /* pool reserved now                                      */
+  double mean_batch;            /* requests per batch                                     */
+  double p50_us, p99_us, mean_us, max_us;  /* submit-to-result latency of completed requests */
+} sieve_server_stats;
+
+/* Start a server on ctx (config NULL: defaults with no pool, i.e. count mode
+ * only).  Errors: INVALID, OOM, CUDA. */
+int sieve_server_start(sieve_ctx *ctx, const sieve_server_config *config, sieve_server **srv);
+/* Admit one query; *req_id identifies it.  INVALID / RANGE for a bad query,
+ * CAPACITY if its list could never fit the pool, BUSY for backpressure. */
+int sieve_server_submit(sieve_server *srv, uint64_t lo, uint64_t hi, int mode, uint64_t *req_id);
+/* SIEVE_PENDING while the request is queued or on the GPU.  When done: fills
+ * *cnt (may be NULL) and *n_out (may be NULL), copies a list-mode answer to
+ * out[0..n) (host memory, or device memory with SIEVE_OUT_DEVICE), releases
+ * the request and returns SIEVE_OK.  A too-small cap returns CAPACITY with
+ * *n_out set and keeps the request for another poll.  NOT_FOUND for an unknown
+ * or already collected id. */
+int sieve_server_poll(sieve_server *srv, uint64_t req_id, sieve_count_result *cnt, uint64_t *out, size_t cap,
+                      size_t *n_out, unsigned flags);
+/* Id of a request that finished since the last call (in completion order),
+ * waiting up to timeout_us microseconds; SIEVE_PENDING if none. */
+int sieve_server_next_done(sieve_server *srv, uint64_t *req_id, int timeout_us);
+/* Counters and latency percentiles; reset != 0 clears them afterwards. */
+int sieve_server_get_stats(sieve_server *srv, sieve_server_stats *st, int reset);
+/* Finish every admitted request, then stop the thread and free the server
+ * (uncollected results are dropped).  NULL is ignored. */
+void sieve_server_stop(sieve_server *srv);
+
 /* ------------------------------------------------------------- no allocation */
 
 /* Size of the fixed device scratch array used by sieve_range_list_noalloc. */

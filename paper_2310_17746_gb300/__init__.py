@@ -7,8 +7,8 @@ raises if that fails -- there is no CPU fallback.
 """
 from __future__ import annotations
 
-from .binding import (ASYNC, COUNT, LIST, OUT_DEVICE, CountAndSum, Sieve, SieveError, last_error,
+from .binding import (ASYNC, COUNT, LIST, OUT_DEVICE, CountAndSum, Server, Sieve, SieveError, last_error,
                       lib, table1_start)
 
-__all__ = ["Sieve", "SieveError", "CountAndSum", "COUNT", "LIST", "OUT_DEVICE", "ASYNC",
-           "lib", "last_error", "table1_start", "workloads"]
+__all__ = ["Sieve", "Server", "SieveError", "CountAndSum", "COUNT", "LIST", "OUT_DEVICE", "ASYNC",
+           "lib", "last_error", "table1_start", "workloads", "shard"]

@@ -60,6 +60,22 @@ class Options(ctypes.Structure):
                 "chunk_primes": self.chunk_primes}
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("pool_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_size_t),
+                ("max_queue", ctypes.c_size_t), ("batch_scratch_bytes", ctypes.c_size_t)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("overlapped_batches", ctypes.c_uint64), ("queued", ctypes.c_uint64),
+                ("pool_used_bytes", ctypes.c_uint64), ("mean_batch", ctypes.c_double),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
+                ("max_us", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _u64 = ctypes.c_uint64
 _sz = ctypes.c_size_t
 _p = ctypes.c_void_p
@@ -88,6 +104,12 @@ SIGNATURES = {
     "sieve_range_each": (_i, [_p, _p, _p, _p, _sz, _p, _p, _p, _sz, ctypes.POINTER(_sz), _u]),
     "sieve_autotune_batch": (_i, [_p, _p, _p, _p, _sz, _i, ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_double)]),
     "sieve_autotune_range": (_i, [_p, _u64, _u64, _i, ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_double)]),
+    "sieve_server_start": (_i, [_p, ctypes.POINTER(ServerConfig), ctypes.POINTER(_p)]),
+    "sieve_server_submit": (_i, [_p, _u64, _u64, _i, ctypes.POINTER(_u64)]),
+    "sieve_server_poll": (_i, [_p, _u64, _p, _p, _sz, ctypes.POINTER(_sz), _u]),
+    "sieve_server_next_done": (_i, [_p, ctypes.POINTER(_u64), _i]),
+    "sieve_server_get_stats": (_i, [_p, ctypes.POINTER(ServerStats), _i]),
+    "sieve_server_stop": (None, [_p]),
 }
 
 
@@ -378,3 +400,93 @@ class Sieve:
         _check(self._lib.sieve_segment_counts(self._h, int(lo), int(hi), int(seg_width), counts.ctypes.data, nb,
                                               ctypes.cast(ctypes.byref(r), _p), 0), "sieve_segment_counts")
         return CountAndSum(r.count, r.checksum), counts[:nb]
+
+
+class Server:
+    """Request loop with continuous batching on a Sieve context (sieve_server_*).
+
+    While a server runs, make no other call on its context."""
+
+    def __init__(self, sieve: Sieve, pool_bytes: int = 1 << 30, max_batch: int = 0, max_queue: int = 0,
+                 batch_scratch_bytes: int = 0):
+        self._lib = lib()
+        self.sieve = sieve
+        cfg = ServerConfig(int(pool_bytes), int(max_batch), int(max_queue), int(batch_scratch_bytes))
+        h = _p()
+        _check(self._lib.sieve_server_start(sieve.handle, ctypes.byref(cfg), ctypes.byref(h)), "sieve_server_start")
+        self._h = h
+
+    def submit(self, lo: int, hi: int, mode: int) -> int:
+        """Admit one query and return its id (SieveError with ERR_BUSY on backpressure)."""
+        rid = _u64(0)
+        _check(self._lib.sieve_server_submit(self._h, int(lo), int(hi), int(mode), ctypes.byref(rid)),
+               "sieve_server_submit")
+        return int(rid.value)
+
+    def try_submit(self, lo: int, hi: int, mode: int):
+        """Like submit, but None instead of an exception when the server is busy."""
+        rid = _u64(0)
+        rc = self._lib.sieve_server_submit(self._h, int(lo), int(hi), int(mode), ctypes.byref(rid))
+        if rc == ERR_BUSY:
+            return None
+        _check(rc, "sieve_server_submit")
+        return int(rid.value)
+
+    def poll(self, rid: int, out=None):
+        """None while pending; else (CountAndSum, primes or None) and the
+        request is released.  `out` (numpy uint64 or torch CUDA int64) receives
+        a list-mode answer; without it a numpy array is returned."""
+        r = CountResult()
+        n = _sz(0)
+        if out is not None:
+            ptr, flags = _ptr_and_flag(out)
+            cap = out.numel() if _is_torch_cuda(out) else out.size
+            rc = self._lib.sieve_server_poll(self._h, int(rid), ctypes.cast(ctypes.byref(r), _p), ptr, cap,
+                                             ctypes.byref(n), flags)
+            if rc == PENDING:
+                return None
+            _check(rc, "sieve_server_poll")
+            return CountAndSum(r.count, r.checksum), int(n.value)
+        rc = self._lib.sieve_server_poll(self._h, int(rid), ctypes.cast(ctypes.byref(r), _p), None, 0,
+                                         ctypes.byref(n), 0)
+        if rc == PENDING:
+            return None
+        if rc == ERR_CAPACITY and n.value > 0:
+            buf = np.empty(int(n.value), dtype=np.uint64)
+            rc = self._lib.sieve_server_poll(self._h, int(rid), ctypes.cast(ctypes.byref(r), _p),
+                                             buf.ctypes.data, buf.size, ctypes.byref(n), 0)
+            _check(rc, "sieve_server_poll")
+            return CountAndSum(r.count, r.checksum), buf
+        _check(rc, "sieve_server_poll")
+        return CountAndSum(r.count, r.checksum), None
+
+    def next_done(self, timeout_us: int = 0):
+        """Id of a finished request, or None if none finished within timeout_us."""
+        rid = _u64(0)
+        rc = self._lib.sieve_server_next_done(self._h, ctypes.byref(rid), int(timeout_us))
+        if rc == PENDING:
+            return None
+        _check(rc, "sieve_server_next_done")
+        return int(rid.value)
+
+    def stats(self, reset: bool = False) -> dict:
+        st = ServerStats()
+        _check(self._lib.sieve_server_get_stats(self._h, ctypes.byref(st), int(bool(reset))), "sieve_server_get_stats")
+        return st.as_dict()
+
+    def stop(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.sieve_server_stop(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.stop()
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass

@@ -420,7 +420,7 @@ extern "C" int sieve_base_table(const sieve_ctx *ctx, uint64_t *limit, uint64_t 
   return SIEVE_OK;
 }
 
-extern "C" uint64_t sieve_launch_count(const sieve_ctx *ctx) { return ctx ? ctx->launches : 0; }
+extern "C" uint64_t sieve_launch_count(const sieve_ctx *ctx) { return ctx ? ctx->launches.load() : 0; }
 
 extern "C" const char *sieve_last_error(void) { return g_err; }
 

@@ -60,6 +60,7 @@ extern "C" int sieve_autotune_batch(sieve_ctx *ctx, const uint64_t *lo, const ui
     size_t need = 0;
     rc = sieve_range_batch(ctx, lo, hi, mode, nq, d_cnt, d_off, nullptr, 0, &need, SIEVE_OUT_DEVICE);
     if (rc != SIEVE_OK && rc != SIEVE_ERR_CAPACITY) break;
+    rc = SIEVE_OK;
     if ((e = cudaMalloc(&d_val, std::max<size_t>(need, 1) * sizeof(uint64_t))) != cudaSuccess) {
       rc = cuda_fail(e, "autotune allocation");
       break;

@@ -92,7 +92,11 @@ __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK > 0 ? 1024 / BLOCK : 1)) 
   uint2 *starts = (uint2 *)(smem + 2 * a.Wmax);
 
   for (;;) {
-    if (threadIdx.x == 0) sh_idx = atomicAdd(&a.state->next_item, 1u);
+    if (threadIdx.x == 0) {
+      const bool yield = 2 * blockIdx.x >= gridDim.x &&
+                         *(volatile const uint32_t *)&a.state->yield_batch == hdr->batch_id;
+      sh_idx = yield ? nitems : atomicAdd(&a.state->next_item, 1u);
+    }
     __syncthreads();
     const uint32_t idx = sh_idx;
     if (idx >= nitems) break;
@@ -261,6 +265,7 @@ template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) batch_compact_kernel(const BatchArena a) {
   constexpr int NWARPS = BLOCK / 32;
   __shared__ uint64_t warp_base[NWARPS];
+  extern __shared__ __align__(16) uint2 sbuf[];  // one tile's bitmap (up to Wmax pairs)
   const char *plan = (const char *)a.plan;
   const BatchHeader *hdr = (const BatchHeader *)plan;
   const uint32_t n = hdr->nltiles;
@@ -294,46 +299,12 @@ __global__ void __launch_bounds__(BLOCK) batch_compact_kernel(const BatchArena a
       off += e2 + e3;
     }
     compact_tile<BLOCK, uint64_t>(a.list_bm + qd.bitmap_off + (uint64_t)qt.y * W, logW, units, chunk_bits, K0, off,
-                                  out, warp_base);
+                                  out, warp_base, sbuf);
     __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------- host: runner
-
-struct BatchRunner {
-  sieve_ctx *ctx = nullptr;
-  cudaStream_t stream = nullptr;
-  // launch shape, fixed for one graph
-  int threads = 0, grid = 0, finish_grid = 0;
-  size_t smem = 0, finish_smem = 0;
-  uint32_t logLmax = 0, Wmax = 0, band_max = 0;
-  // device capacities (elements of each buffer)
-  size_t plan_cap = 0, acc_cap = 0, offsets_cap = 0, slot_cap = 0, counts_cap = 0, toff_cap = 0, list_cap = 0;
-  char *d_plan = nullptr;
-  BatchState *d_state = nullptr;
-  unsigned long long *d_acc = nullptr;
-  uint32_t *d_slot_bm = nullptr, *d_tile_counts = nullptr;
-  uint64_t *d_tile_off = nullptr, *d_offsets = nullptr;
-  uint2 *d_list_bm = nullptr;
-  // pinned host plan and read-back words
-  char *h_plan = nullptr;
-  size_t h_plan_cap = 0;
-  uint64_t *h_back = nullptr;  // [0] status, [1] list total
-  // graph
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  cudaGraphNode_t n_copy = nullptr;
-  // planning scratch
-  std::vector<BatchQuery> q;
-  std::vector<BatchItem> items, sorted;
-  std::vector<float> cost;
-  std::vector<uint2> mtiles, ltiles;
-  std::vector<uint32_t> ltile0;
-  uint64_t slot_words = 0, list_words = 0;
-  size_t plan_bytes = 0;
-  uint32_t used_logW = 0;  // bit mask of tile widths in the plan
-};
 
 void destroy_batch_runner(BatchRunner *r) {
   if (!r) return;
@@ -402,7 +373,7 @@ void *sieve_kernel_fn(int threads) {
 }
 
 constexpr int kFinishThreads = 256;
-constexpr int kCompactThreads = 256;
+constexpr int kCompactThreads = 512;
 constexpr int kScanThreads = 1024;
 
 // Launch shape for the context's current options: threads, largest tile,
@@ -426,6 +397,8 @@ int configure(BatchRunner &r) {
   void *fn = sieve_kernel_fn(threads);
   SIEVE_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->smem_optin));
   SIEVE_CUDA_TRY(cudaFuncSetAttribute((void *)batch_finish_kernel<kFinishThreads>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->smem_optin));
+  SIEVE_CUDA_TRY(cudaFuncSetAttribute((void *)batch_compact_kernel<kCompactThreads>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->smem_optin));
   int per_sm = 0, fper_sm = 0;
   SIEVE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
@@ -493,8 +466,9 @@ int build_graph(BatchRunner &r) {
   kp.sharedMemBytes = 0;
   SIEVE_CUDA_TRY(cudaGraphAddKernelNode(&n_scan, g, &n_finish, 1, &kp));
   kp.func = (void *)batch_compact_kernel<kCompactThreads>;
-  kp.gridDim = dim3(r.ctx->num_sms * 4);
+  kp.gridDim = dim3(r.ctx->num_sms * 2);
   kp.blockDim = dim3(kCompactThreads);
+  kp.sharedMemBytes = (unsigned)((size_t)r.Wmax * sizeof(uint2));
   SIEVE_CUDA_TRY(cudaGraphAddKernelNode(&n_compact, g, &n_scan, 1, &kp));
   SIEVE_CUDA_TRY(cudaGraphInstantiate(&r.exec, g, 0));
   r.n_copy = n_copy;
@@ -515,16 +489,47 @@ namespace {
 // (Mertens' second theorem).
 double lnln(double x) { return std::log(std::log(std::max(x, 23.0))); }
 
-// Relative cost units of the work an item does (one unit ~ one strike).
+// Relative cost units of the work an item does (one unit ~ one strike in
+// shared memory).  An atomic AND in global memory is priced at many strikes:
+// the merge bitmaps of a batch rarely stay in L2, so each costs a DRAM
+// read-modify-write of a 32-byte sector.
 constexpr double kCostItem = 4000.0;   // fixed per item: barriers, set-up
 constexpr double kCostPrime = 10.0;    // one Table 1 evaluation
 constexpr double kCostWord = 6.0;      // presieve copy + count of one word pair
-constexpr double kCostGlobal = 4.0;    // one atomic AND in global memory
+constexpr double kCostGlobal = 40.0;   // one atomic AND in global memory (L2-resident bitmap)
+constexpr double kL2Bitmap = 48e6;     // a merged query's bitmap above this many bytes
+                                       // spills from L2: its atomics cost 4x
+constexpr uint32_t kMinChunk = 256;    // fewest primes in a split piece of a tile
 
 struct QueryPlanInfo {
   uint32_t np = 0, i_mid = 0;
-  bool merged = false;
+  bool strips = false;  // primes [i_mid, np) go to strip items
+  double tile_cost = 0.0;
+  double gcost = 0.0;   // cost of one global atomic for this query's bitmap
+  double total = 0.0;   // all items of the query
 };
+
+// Cost of striking primes [a, b) into a tile of L indices per class.
+double tile_primes_cost(const uint32_t *P, uint32_t a, uint32_t b, uint32_t L) {
+  if (b <= a) return 0.0;
+  return kCostPrime * (b - a) + 2.0 * (double)L * (lnln((double)P[b - 1]) - lnln((double)P[a]));
+}
+
+// Largest n in [1, cap] with cost(n) <= target (1 if even cost(1) is above);
+// cost must grow with n.
+template <typename F>
+uint32_t largest_within(uint32_t cap, double target, F cost) {
+  if (cost(cap) <= target) return cap;
+  uint32_t lo = 1, hi = cap;
+  while (lo < hi) {
+    const uint32_t mid = lo + (hi - lo + 1) / 2;
+    if (cost(mid) <= target)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
 
 }  // namespace
 
@@ -608,29 +613,29 @@ int batch_plan(BatchRunner &r, const uint64_t *lo, const uint64_t *hi, const uin
     uint32_t i_split = host_prime_count_le_table(table, L / (32ull * gh));
     if (i_split < i_first) i_split = i_first;
     bq.i_split = i_split;
-    // merged when the primes above the tile length, repeated over the tiles,
-    // are worth locating once per query instead of once per tile
+    // Primes above the tile length hit a tile at most twice.  Strips locate
+    // them once per query and clear each hit with a global atomic; tiles
+    // locate them once per tile.  Strips are taken when they cost less.
     uint32_t i_mid = host_prime_count_le_table(table, L);
     if (i_mid < i_first) i_mid = i_first;
     QueryPlanInfo &qi = info[i];
     qi.np = np;
     qi.i_mid = i_mid;
-    qi.merged = np > i_mid && (uint64_t)(np - i_mid) * ntiles >= chunk && span < (1ull << 31);
-    if (qi.merged) {
-      bq.flags |= kQueryMerged;
-      bq.slot_base = r.slot_words;
-      r.slot_words += ntiles * 2ull * (L / 32);
-    }
+    const double pm = (double)P[std::min(i_mid, table.nprimes - 1)];
+    const double hits = np > i_mid ? 2.0 * (double)span * (lnln((double)P[np - 1]) - lnln(pm)) : 0.0;
+    const double large = np > i_mid ? (double)(np - i_mid) : 0.0;
+    qi.gcost = (double)span / 4.0 > kL2Bitmap ? 4.0 * kCostGlobal : kCostGlobal;
+    qi.strips = ntiles >= 2 && span < (1ull << 31) && np > i_mid &&
+                kCostPrime * large + qi.gcost * hits < kCostPrime * large * (double)ntiles;
+    const uint32_t t_end = qi.strips ? i_mid : std::max(np, i_first);
+    qi.tile_cost = kCostItem + kCostWord * (L / 32) + tile_primes_cost(P, i_first, t_end, L);
+    total_cost += (double)ntiles * qi.tile_cost;
+    if (qi.strips) total_cost += kCostPrime * large + qi.gcost * hits;
     if (bq.flags & kQueryList) {
       bq.bitmap_off = r.list_words;
       r.list_words += ntiles * (uint64_t)(L / 32);
       nlt += (uint32_t)ntiles;
     }
-    // cost estimate for the item size target
-    const double pn = np ? (double)P[np - 1] : 23.0;
-    const double pf = np > i_first ? (double)P[i_first] : 23.0;
-    total_cost += (double)ntiles * (kCostItem + kCostWord * (L / 32)) + kCostPrime * (np > i_first ? np - i_first : 0) +
-                  2.0 * (double)span * (lnln(pn) - lnln(pf));
   }
   r.ltile0[nq] = nlt;
   // target cost per item: a few items per CTA slot so that the cost-ordered
@@ -638,46 +643,52 @@ int batch_plan(BatchRunner &r, const uint64_t *lo, const uint64_t *hi, const uin
   const double target = std::max(total_cost / ((double)r.grid * 4.0), 2.0e5);
 
   for (size_t i = 0; i < nq; i++) {
-    const BatchQuery &bq = r.q[i];
+    BatchQuery &bq = r.q[i];
     if (bq.ntiles == 0) continue;
     const QueryPlanInfo &qi = info[i];
     const uint32_t L = 1u << bq.logL, W = L / 32;
     const uint64_t span = bq.k_end - bq.k_begin;
-    const uint32_t t_end = qi.merged ? qi.i_mid : std::max(qi.np, i_first);
-    const double p_lo = (double)P[std::min<uint32_t>(i_first, table.nprimes - 1)];
-    const double p_hi = t_end > i_first ? (double)P[t_end - 1] : p_lo;
-    const double tile_cost = kCostItem + kCostWord * W + kCostPrime * (t_end - i_first) +
-                             2.0 * (double)L * (lnln(p_hi) - lnln(p_lo));
+    const uint32_t t_end = qi.strips ? qi.i_mid : std::max(qi.np, i_first);
+    // a tile too costly for one item is split by primes into pieces that
+    // different CTAs sieve in shared memory and AND into global memory
+    const bool split = qi.tile_cost > target && t_end - i_first >= 2 * kMinChunk;
+    if (qi.strips || split) {
+      bq.flags |= kQueryMerged;
+      bq.slot_base = r.slot_words;
+      r.slot_words += (uint64_t)bq.ntiles * 2ull * W;
+    }
+    const double fixed = kCostItem + kCostWord * W;
     for (uint32_t t = 0; t < bq.ntiles; t++) {
-      r.items.push_back(BatchItem{(uint32_t)i, t, i_first, t_end});
-      r.cost.push_back((float)tile_cost);
-      if (qi.merged) r.mtiles.push_back(make_uint2((uint32_t)i, t));
+      if (!split) {
+        r.items.push_back(BatchItem{(uint32_t)i, t, i_first, t_end});
+        r.cost.push_back((float)qi.tile_cost);
+      } else {
+        uint32_t a = i_first;
+        while (a < t_end) {
+          const uint32_t cap = std::min<uint32_t>(chunk, t_end - a);
+          uint32_t n = largest_within(cap, target, [&](uint32_t k) { return fixed + tile_primes_cost(P, a, a + k, L); });
+          if (n < kMinChunk) n = std::min<uint32_t>(kMinChunk, t_end - a);
+          r.items.push_back(BatchItem{(uint32_t)i, t, a, a + n});
+          r.cost.push_back((float)(fixed + tile_primes_cost(P, a, a + n, L)));
+          a += n;
+        }
+      }
+      if (bq.flags & kQueryMerged) r.mtiles.push_back(make_uint2((uint32_t)i, t));
       if (bq.flags & kQueryList) r.ltiles.push_back(make_uint2((uint32_t)i, t));
     }
-    if (qi.merged) {
+    if (qi.strips) {
       // strips of primes [i_mid, np): at most `chunk` primes and about
       // `target` cost each
       uint32_t a = qi.i_mid;
       while (a < qi.np) {
         const double la = lnln((double)P[a]);
-        uint32_t lo_n = 1, hi_n = std::min<uint32_t>(chunk, qi.np - a);
         auto strip_cost = [&](uint32_t n) {
-          return kCostItem + kCostPrime * n + kCostGlobal * 2.0 * (double)span * (lnln((double)P[a + n - 1]) - la);
+          return kCostItem + kCostPrime * n + qi.gcost * 2.0 * (double)span * (lnln((double)P[a + n - 1]) - la);
         };
-        if (strip_cost(hi_n) <= target) {
-          lo_n = hi_n;
-        } else {
-          while (lo_n < hi_n) {  // largest n with cost <= target (at least 1)
-            const uint32_t mid = lo_n + (hi_n - lo_n + 1) / 2;
-            if (strip_cost(mid) <= target)
-              lo_n = mid;
-            else
-              hi_n = mid - 1;
-          }
-        }
-        r.items.push_back(BatchItem{(uint32_t)i, kStrip, a, a + lo_n});
-        r.cost.push_back((float)strip_cost(lo_n));
-        a += lo_n;
+        const uint32_t n = largest_within(std::min<uint32_t>(chunk, qi.np - a), target, strip_cost);
+        r.items.push_back(BatchItem{(uint32_t)i, kStrip, a, a + n});
+        r.cost.push_back((float)strip_cost(n));
+        a += n;
       }
     }
   }
@@ -688,13 +699,18 @@ int batch_plan(BatchRunner &r, const uint64_t *lo, const uint64_t *hi, const uin
 
   // cost order (largest first) by a counting sort on log2 buckets: items
   // that cost more start earlier, so the queue drains evenly (longest
-  // processing time first)
+  // processing time first).  The items of a merged query share one key (the
+  // query's total), so they run together and its bitmap in global memory
+  // stays in L2 while it is struck.
   const size_t ni = r.items.size();
+  for (size_t j = 0; j < ni; j++) info[r.items[j].q].total += r.cost[j];
   constexpr int kBuckets = 128;
   size_t bucket_n[kBuckets + 1] = {0};
   std::vector<uint8_t> bk(ni);
   for (size_t j = 0; j < ni; j++) {
-    int b = (int)(4.0f * std::log2(std::max(r.cost[j], 1.0f)));
+    const uint32_t qj = r.items[j].q;
+    const float key = (r.q[qj].flags & kQueryMerged) ? (float)info[qj].total : r.cost[j];
+    int b = (int)(4.0f * std::log2(std::max(key, 1.0f)));
     b = std::min(std::max(b, 0), kBuckets - 1);
     bk[j] = (uint8_t)(kBuckets - 1 - b);
     bucket_n[bk[j] + 1]++;
@@ -726,6 +742,8 @@ int batch_plan(BatchRunner &r, const uint64_t *lo, const uint64_t *hi, const uin
   h.cap = cap;
   h.fixed_out = fixed_out ? 1u : 0u;
   h.npat = 1u + ctx->opt.presieve_groups;
+  r.batch_id = r.batch_id == 0xFFFFFFFFu ? 1u : r.batch_id + 1;
+  h.batch_id = r.batch_id;
   r.plan_bytes = off;
   if (off > r.h_plan_cap) {
     if (r.h_plan) {
@@ -772,6 +790,10 @@ int batch_prepare(BatchRunner &r) {
   if ((rc = grow_device(&r.d_list_bm, &r.list_cap, (size_t)r.list_words + 1, &changed)) != SIEVE_OK) return rc;
   if (!r.d_state) {
     SIEVE_CUDA_TRY(cudaMalloc(&r.d_state, sizeof(BatchState)));
+    // yield_batch = 0 (no batch id); complete before any yield request can
+    // be written from another stream
+    SIEVE_CUDA_TRY(cudaMemsetAsync(r.d_state, 0, sizeof(BatchState), r.stream));
+    SIEVE_CUDA_TRY(cudaStreamSynchronize(r.stream));
     changed = true;
   }
   if (!r.h_back) SIEVE_CUDA_TRY(cudaMallocHost((void **)&r.h_back, 4 * sizeof(uint64_t)));
@@ -786,6 +808,41 @@ int batch_prepare(BatchRunner &r) {
     r.graph = nullptr;
   }
   return build_graph(r);
+}
+
+// Allocate a runner's buffers up front for batches of up to nq queries,
+// `items` work items, `slot_words` merge-bitmap words and `list_words` list
+// bitmap pairs, so that planning such batches never grows (and so never
+// frees, which would synchronise the device) a buffer.
+int batch_reserve(BatchRunner &r, size_t nq, size_t items, uint64_t slot_words, uint64_t list_words) {
+  bool changed = false;
+  int rc;
+  const size_t ltiles = (size_t)(list_words / 32) + nq + 1;
+  const size_t plan = align256(sizeof(BatchHeader)) + align256(nq * sizeof(BatchQuery)) +
+                      align256(items * sizeof(BatchItem)) + 2 * align256(ltiles * sizeof(uint2)) +
+                      align256((nq + 1) * sizeof(uint32_t));
+  if ((rc = grow_device(&r.d_plan, &r.plan_cap, plan, &changed)) != SIEVE_OK) return rc;
+  if ((rc = grow_device(&r.d_acc, &r.acc_cap, 2 * nq + 2, &changed)) != SIEVE_OK) return rc;
+  if ((rc = grow_device(&r.d_offsets, &r.offsets_cap, nq + 1, &changed)) != SIEVE_OK) return rc;
+  if ((rc = grow_device(&r.d_slot_bm, &r.slot_cap, (size_t)slot_words + 4, &changed)) != SIEVE_OK) return rc;
+  if ((rc = grow_device(&r.d_tile_counts, &r.counts_cap, ltiles, &changed)) != SIEVE_OK) return rc;
+  if ((rc = grow_device(&r.d_tile_off, &r.toff_cap, ltiles, &changed)) != SIEVE_OK) return rc;
+  if ((rc = grow_device(&r.d_list_bm, &r.list_cap, (size_t)list_words + 1, &changed)) != SIEVE_OK) return rc;
+  if (plan > r.h_plan_cap) {
+    if (r.h_plan) cudaFreeHost(r.h_plan);
+    r.h_plan = nullptr;
+    r.h_plan_cap = 0;
+    SIEVE_CUDA_TRY(cudaMallocHost((void **)&r.h_plan, plan));
+    r.h_plan_cap = plan;
+    changed = true;
+  }
+  if (changed && r.exec) {
+    cudaGraphExecDestroy(r.exec);
+    r.exec = nullptr;
+    cudaGraphDestroy(r.graph);
+    r.graph = nullptr;
+  }
+  return SIEVE_OK;
 }
 
 // Launch the planned batch on r.stream (asynchronous).
@@ -819,7 +876,8 @@ int batch_recompact(BatchRunner &r, uint64_t *values, uint64_t cap) {
   SIEVE_CUDA_TRY(cudaMemcpyAsync(r.d_plan + offsetof(BatchHeader, values), r.h_back + 2, sizeof(patch),
                                  cudaMemcpyHostToDevice, r.stream));
   BatchArena a = arena_of(r);
-  batch_compact_kernel<kCompactThreads><<<r.ctx->num_sms * 4, kCompactThreads, 0, r.stream>>>(a);
+  batch_compact_kernel<kCompactThreads>
+      <<<r.ctx->num_sms * 2, kCompactThreads, (size_t)r.Wmax * sizeof(uint2), r.stream>>>(a);
   r.ctx->launches++;
   SIEVE_CUDA_TRY(cudaGetLastError());
   return SIEVE_OK;

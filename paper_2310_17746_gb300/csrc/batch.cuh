@@ -25,6 +25,8 @@
 // kernel waits on another CTA).
 #pragma once
 
+#include <vector>
+
 #include "sieve_internal.cuh"
 
 namespace sieve {
@@ -61,12 +63,20 @@ struct BatchHeader {
   uint64_t cap;          // CSR mode: capacity of values
   uint32_t fixed_out;    // 0: CSR (query q at offsets[q]); 1: query q at out_base
   uint32_t npat;         // presieve patterns in use
+  uint32_t batch_id;     // distinct for every launch of a runner (see BatchState)
+  uint32_t pad_;
 };
 
 // Device-written state of one batch.
 struct BatchState {
   uint32_t next_item;
-  uint32_t status;  // bit 0: CSR capacity exceeded; bit 1: a query exceeded its out_cap
+  uint32_t status;       // bit 0: CSR capacity exceeded; bit 1: a query exceeded its out_cap
+  uint32_t yield_batch;  // when it equals the running batch's id, CTAs in the upper half of
+                         // the grid take no further item and exit, making room for another
+                         // batch (the lower half finishes the queue).  Written by the host
+                         // at any time; never reset by the batch, so an early or late write
+                         // for another batch id has no effect.
+  uint32_t pad_;
 };
 
 // Device buffers of a batch arena (kernel parameters; fixed for a graph).
@@ -85,5 +95,52 @@ struct BatchArena {
   uint32_t Wmax;               // words per class of the largest tile
   uint32_t band_max;           // warp-band start slots in shared memory
 };
+
+// Host side of one batch arena: its device buffers, pinned plan, CUDA graph
+// and planning scratch (batch.cu).  A runner launches on its own stream; a
+// plan may be rebuilt only once the runner's previous launch has completed.
+struct BatchRunner {
+  sieve_ctx *ctx = nullptr;
+  cudaStream_t stream = nullptr;
+  // launch shape, fixed for one graph
+  int threads = 0, grid = 0, finish_grid = 0;
+  size_t smem = 0, finish_smem = 0;
+  uint32_t logLmax = 0, Wmax = 0, band_max = 0;
+  // device capacities (elements of each buffer)
+  size_t plan_cap = 0, acc_cap = 0, offsets_cap = 0, slot_cap = 0, counts_cap = 0, toff_cap = 0, list_cap = 0;
+  char *d_plan = nullptr;
+  BatchState *d_state = nullptr;
+  unsigned long long *d_acc = nullptr;
+  uint32_t *d_slot_bm = nullptr, *d_tile_counts = nullptr;
+  uint64_t *d_tile_off = nullptr, *d_offsets = nullptr;
+  uint2 *d_list_bm = nullptr;
+  // pinned host plan and read-back words
+  char *h_plan = nullptr;
+  size_t h_plan_cap = 0;
+  uint64_t *h_back = nullptr;  // [0] status, [1] list total
+  // graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t n_copy = nullptr;
+  // planning scratch
+  std::vector<BatchQuery> q;
+  std::vector<BatchItem> items, sorted;
+  std::vector<float> cost;
+  std::vector<uint2> mtiles, ltiles;
+  std::vector<uint32_t> ltile0;
+  uint64_t slot_words = 0, list_words = 0;
+  size_t plan_bytes = 0;
+  uint32_t used_logW = 0;  // bit mask of tile widths in the plan
+  uint32_t batch_id = 0;   // id of the last planned batch (first is 1)
+};
+
+// Runner operations (batch.cu).
+BatchRunner *new_batch_runner(sieve_ctx *ctx, cudaStream_t stream);
+int batch_configure(BatchRunner &r);
+int batch_plan(BatchRunner &r, const uint64_t *lo, const uint64_t *hi, const uint8_t *mode, size_t nq,
+               uint64_t *values, uint64_t cap, int fixed_out, const uint64_t *out_base, const uint64_t *out_cap);
+int batch_prepare(BatchRunner &r);
+int batch_reserve(BatchRunner &r, size_t nq, size_t items, uint64_t slot_words, uint64_t list_words);
+int batch_launch(BatchRunner &r);
 
 }  // namespace sieve

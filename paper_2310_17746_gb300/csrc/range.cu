@@ -198,6 +198,7 @@ template <int BLOCK, typename OutT>
 __global__ void __launch_bounds__(BLOCK) compact_kernel(const CompactParams p) {
   constexpr int NWARPS = BLOCK / 32;
   __shared__ uint64_t warp_base[NWARPS];
+  extern __shared__ __align__(16) uint2 sbuf[];  // one tile's bitmap (W pairs)
   if (p.offsets[p.ntiles] > p.cap) return;  // capacity: the host reports it
   OutT *out = (OutT *)p.out;
   const uint32_t W = p.L / 32;
@@ -218,12 +219,14 @@ __global__ void __launch_bounds__(BLOCK) compact_kernel(const CompactParams p) {
       }
       off += (p.lo <= 2 && 2 < p.hi) + (p.lo <= 3 && 3 < p.hi);
     }
-    compact_tile<BLOCK, OutT>(bm, p.logW, units, chunk_bits, K0, off, out, warp_base);
+    compact_tile<BLOCK, OutT>(bm, p.logW, units, chunk_bits, K0, off, out, warp_base, sbuf);
     __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------- host side
+
+constexpr int kCompactBlock = 512;
 
 namespace {
 
@@ -279,6 +282,10 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 int range_set_smem_attributes(int bytes) {
   int rc;
+  SIEVE_CUDA_TRY(cudaFuncSetAttribute(compact_kernel<kCompactBlock, uint32_t>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  SIEVE_CUDA_TRY(cudaFuncSetAttribute(compact_kernel<kCompactBlock, uint64_t>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   if ((rc = set_smem_attr<256>(bytes)) != SIEVE_OK) return rc;
   if ((rc = set_smem_attr<512>(bytes)) != SIEVE_OK) return rc;
   return set_smem_attr<1024>(bytes);
@@ -523,11 +530,12 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
   cp.offsets = offsets;
   cp.out = dst;
   cp.cap = req.cap;
+  const size_t csmem = (size_t)(L / 32) * sizeof(uint2);
   const int cgrid = (int)std::min<uint64_t>(ntiles, (uint64_t)ctx->num_sms * 4);
   if (req.out_bytes == 4)
-    compact_kernel<256, uint32_t><<<cgrid, 256, 0, st>>>(cp);
+    compact_kernel<kCompactBlock, uint32_t><<<cgrid, kCompactBlock, csmem, st>>>(cp);
   else
-    compact_kernel<256, uint64_t><<<cgrid, 256, 0, st>>>(cp);
+    compact_kernel<kCompactBlock, uint64_t><<<cgrid, kCompactBlock, csmem, st>>>(cp);
   ctx->launches++;
   SIEVE_CUDA_TRY(cudaGetLastError());
   if (!dev_out)
@@ -675,7 +683,7 @@ int run_range_list_into(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *out,
   cp.out = out;
   cp.cap = cap;
   const int cgrid = (int)std::min<uint64_t>(ntiles, (uint64_t)ctx->num_sms * 4);
-  compact_kernel<256, uint64_t><<<cgrid, 256, 0, st>>>(cp);
+  compact_kernel<kCompactBlock, uint64_t><<<cgrid, kCompactBlock, (size_t)(L / 32) * sizeof(uint2), st>>>(cp);
   ctx->launches++;
   SIEVE_CUDA_TRY(cudaGetLastError());
   SIEVE_CUDA_TRY(cudaStreamSynchronize(st));

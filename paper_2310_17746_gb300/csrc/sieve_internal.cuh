@@ -9,6 +9,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -143,20 +144,25 @@ __host__ __device__ __forceinline__ StartIndex table1_start(uint64_t B, uint64_t
   return s;
 }
 
-// Table 1 start indices for a tile with base B, start value M = B, and a
-// prime P with P^2 <= B and P < 2^31: Q = B - u with u = 1 + ((B - 1) mod P)
-// in [1, P], so the index near Q is I = floor(-u / 6) = -ceil(u / 6) and
-// q = Q mod 6 = (-u) mod 6; everything after the one 64-bit remainder is
-// 32-bit.  The sum I + a R' + b is formed modulo 2^32 (unsigned, so that the
-// wrap is defined); the start itself is in [0, 2^32) for P < 2^31, so the
-// result is exact.  Same result as table1_start(B, B, P, m).
-__host__ __device__ __forceinline__ void table1_start_tile(uint64_t B, uint32_t P, uint64_t m, uint32_t &id1,
-                                                           uint32_t &id5) {
+// u = 1 + ((B - 1) mod P), in [1, P]: B - u is the greatest multiple of P
+// below B (the Q of Table 1 for a segment starting at M = B), and the first
+// multiple at or above B is B + (P - u).  One 64-bit remainder by the
+// reciprocal m of P.
+__host__ __device__ __forceinline__ uint32_t dist_below(uint64_t B, uint32_t P, uint64_t m) {
   const uint64_t n = B - 1;
   const uint64_t qq = mulhi64(n, m);
   uint32_t r = (uint32_t)(n - qq * (uint64_t)P);
   if (r >= P) r -= P;
-  const uint32_t u = r + 1;
+  return r + 1;
+}
+
+// Table 1 start indices for a tile with base B, start value M = B, and a
+// prime P with P^2 <= B and P < 2^31, from u = dist_below(B, P, m): the index
+// near Q = B - u is I = floor(-u / 6) = -ceil(u / 6) and q = Q mod 6 =
+// (-u) mod 6; everything is 32-bit.  The sum I + a R' + b is formed modulo 2^32
+// (unsigned, so that the wrap is defined); the start itself is in [0, 2^32)
+// for P < 2^31, so the result is exact.  Same result as table1_start(B, B, P, m).
+__host__ __device__ __forceinline__ void table1_from_dist(uint32_t u, uint32_t P, uint32_t &id1, uint32_t &id5) {
   const uint32_t cu = (u + 5) / 6;
   const uint32_t q = 6 * cu - u;
   const uint32_t R = P / 6u;
@@ -178,6 +184,11 @@ __host__ __device__ __forceinline__ void table1_start_tile(uint64_t B, uint32_t 
   id5 = a5 * Rp + b5 - cu;
 }
 
+__host__ __device__ __forceinline__ void table1_start_tile(uint64_t B, uint32_t P, uint64_t m, uint32_t &id1,
+                                                           uint32_t &id5) {
+  table1_from_dist(dist_below(B, P, m), P, id1, id5);
+}
+
 // Start indices of prime P in the tile with base B (M = B), as uint64 (every
 // start is >= 0): the 32-bit path when P^2 <= B and P < 2^31, else the
 // general one.  The kernels and the host entry sieve_table1_start use this.
@@ -194,6 +205,28 @@ __host__ __device__ __forceinline__ void tile_starts(uint64_t B, uint32_t P, uin
     k1 = (uint64_t)st.id1;
     k5 = (uint64_t)st.id5;
   }
+}
+
+// Start indices of P in a tile with base B whose values end below B + span6,
+// or false when P has no multiple in [B, B + span6) at all: then neither class
+// is hit and the Table 1 step is skipped (the common case for primes larger
+// than a narrow tile).
+__host__ __device__ __forceinline__ bool tile_starts_within(uint64_t B, uint32_t P, uint64_t m, uint32_t span6,
+                                                            uint64_t &k1, uint64_t &k5) {
+  const uint64_t P2 = (uint64_t)P * P;
+  if (P2 <= B && P < 0x80000000u) {
+    const uint32_t u = dist_below(B, P, m);
+    if (P - u >= span6) return false;
+    uint32_t i1, i5;
+    table1_from_dist(u, P, i1, i5);
+    k1 = i1;
+    k5 = i5;
+    return true;
+  }
+  const StartIndex st = table1_start(B, B, P, m);
+  k1 = (uint64_t)st.id1;
+  k5 = (uint64_t)st.id5;
+  return true;
 }
 
 // ---------------------------------------------------------------- context
@@ -229,7 +262,7 @@ struct sieve_ctx {
     sieve::PatternDesc pd[sieve::kNumPatterns];
   } sliced[32];
   sieve_options opt{};
-  uint64_t launches = 0;
+  std::atomic<uint64_t> launches{0};  // read by other threads while a server runs
   // device copy of the pattern sets, indexed by log2(W); entry i is valid
   // when bit i of psets_ready is set
   sieve::PatternSetDev *d_psets = nullptr;

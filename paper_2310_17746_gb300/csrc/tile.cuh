@@ -139,7 +139,7 @@ __device__ __forceinline__ void strike_primes(uint32_t *s1, uint32_t *s5, uint64
                                               uint32_t i_first, uint32_t i_split, uint32_t np, uint32_t *next) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t split = i_split < np ? i_split : np;
-  const uint32_t len = tg.len, wmask = tg.W - 1, logW = tg.logW;
+  const uint32_t len = tg.len, wmask = tg.W - 1, logW = tg.logW, span6 = 6 * tg.len;
   for (;;) {
     uint32_t i = 0;
     if (lane == 0) i = atomicAdd(next, 1u);
@@ -169,9 +169,10 @@ __device__ __forceinline__ void strike_primes(uint32_t *s1, uint32_t *s5, uint64
       mn = __ldg(magic + in);
     }
     uint64_t k1, k5;
-    tile_starts(B, P, m, k1, k5);
-    if (k1 < len) strike(s1, (uint32_t)k1, P, len, wmask, logW);
-    if (k5 < len) strike(s5, (uint32_t)k5, P, len, wmask, logW);
+    if (tile_starts_within(B, P, m, span6, k1, k5)) {
+      if (k1 < len) strike(s1, (uint32_t)k1, P, len, wmask, logW);
+      if (k5 < len) strike(s5, (uint32_t)k5, P, len, wmask, logW);
+    }
     i = in;
     P = Pn;
     m = mn;
@@ -249,23 +250,6 @@ __device__ __forceinline__ uint32_t bit_index_sum(uint32_t x) {
          (__popc(x & 0xFF00FF00u) << 3) + (__popc(x & 0xFFFF0000u) << 4);
 }
 
-// Interleave: bit 2j of the result is bit j of a, bit 2j+1 is bit j of b.
-// With a = class 1 and b = class 5 of one index run, bit order = value order
-// (6k+1 < 6k+5 < 6(k+1)+1).
-__device__ __forceinline__ uint64_t spread_bits(uint32_t x) {
-  uint64_t v = x;
-  v = (v | (v << 16)) & 0x0000FFFF0000FFFFull;
-  v = (v | (v << 8)) & 0x00FF00FF00FF00FFull;
-  v = (v | (v << 4)) & 0x0F0F0F0F0F0F0F0Full;
-  v = (v | (v << 2)) & 0x3333333333333333ull;
-  v = (v | (v << 1)) & 0x5555555555555555ull;
-  return v;
-}
-
-__device__ __forceinline__ uint64_t interleave_classes(uint32_t a, uint32_t b) {
-  return spread_bits(a) | (spread_bits(b) << 1);
-}
-
 template <int BLOCK>
 __device__ __forceinline__ void block_sum3(uint64_t &a, uint64_t &b, uint64_t &c, uint64_t *red) {
   constexpr int NWARPS = BLOCK / 32;
@@ -299,27 +283,41 @@ __device__ __forceinline__ void block_sum3(uint64_t &a, uint64_t &b, uint64_t &c
 // tile's bitmap bm holds W = 2^logW (class-1 word, class-5 word) pairs in the
 // sliced layout.  Row b of the tile is the index run [b W, b W + W); a unit
 // (b, c) is the 32 indices b W + 32 c + j, j = 0..31, and units in row-major
-// order are in value order.  A warp reads the 32 words of chunk c and
-// extracts row b of each class with one ballot (the ballot transposes the
-// bits), interleaves the two classes in value order and lane j writes the
-// values of bits 2j and 2j+1.  Each warp owns a contiguous run of units; a
-// first pass counts them and a block scan (in warp_base, NWARPS entries)
-// places the warps.  Bits outside the valid range must already be clear.
+// order are in value order.  In a unit, lane j reads word 32 c + j, so its
+// own candidates are bit b of its two words: the values 6 k + 1 and 6 k + 5
+// with k = K0 + b W + 32 c + j.  Their rank among the unit's survivors (value
+// order 6k+1 < 6k+5 < 6(k+1)+1) is the number of survivors of lower lanes in
+// both classes -- two ballots and two popcounts -- plus 1 for the 6k+5 value
+// when 6k+1 survives.  Each warp owns a contiguous run of units; a first pass
+// counts them and a block scan (in warp_base, NWARPS entries) places the
+// warps.  The bitmap is first staged in shared memory (sbuf, W entries, with
+// 16-byte loads; bm must be 16-byte aligned) so that both passes read it at
+// shared-memory latency.  Bits outside the valid range must already be clear.
 template <int BLOCK, typename OutT>
 __device__ __forceinline__ void compact_tile(const uint2 *__restrict__ bm, uint32_t logW, uint32_t units,
                                              uint32_t chunk_bits, uint64_t K0, uint64_t off, OutT *out,
-                                             uint64_t *warp_base) {
+                                             uint64_t *warp_base, uint2 *sbuf) {
   constexpr int NWARPS = BLOCK / 32;
+  {
+    const uint4 *src = (const uint4 *)bm;
+    uint4 *dst = (uint4 *)sbuf;
+    for (uint32_t i = threadIdx.x; i < (1u << logW) / 2; i += BLOCK) dst[i] = __ldg(src + i);
+  }
+  __syncthreads();
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lt = (1u << lane) - 1u;  // lanes below this one
+  const uint32_t cmask = (1u << chunk_bits) - 1u;
   const uint32_t per_warp = (units + NWARPS - 1) / NWARPS;
   const uint32_t u_begin = min(warp * per_warp, units);
   const uint32_t u_end = min(u_begin + per_warp, units);
   uint32_t c = 0;
   for (uint32_t u = u_begin; u < u_end; u++) {
-    const uint32_t b = u >> chunk_bits, w = ((u & ((1u << chunk_bits) - 1)) << 5) + lane;
-    const uint2 x = bm[w];
-    c += __popc(__ballot_sync(kFullMask, (x.x >> b) & 1u)) + __popc(__ballot_sync(kFullMask, (x.y >> b) & 1u));
+    const uint32_t b = u >> chunk_bits;
+    const uint2 x = sbuf[((u & cmask) << 5) + lane];
+    c += ((x.x >> b) & 1u) + ((x.y >> b) & 1u);
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFullMask, c, o);
   if (lane == 0) warp_base[warp] = c;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -331,18 +329,19 @@ __device__ __forceinline__ void compact_tile(const uint2 *__restrict__ bm, uint3
     }
   }
   __syncthreads();
-  uint64_t base = warp_base[warp];
+  OutT *o = out + warp_base[warp];
   for (uint32_t u = u_begin; u < u_end; u++) {
-    const uint32_t b = u >> chunk_bits, c0 = (u & ((1u << chunk_bits) - 1)) << 5;
-    const uint2 x = bm[c0 + lane];
-    const uint32_t m1 = __ballot_sync(kFullMask, (x.x >> b) & 1u);
-    const uint32_t m5 = __ballot_sync(kFullMask, (x.y >> b) & 1u);
-    const uint64_t z = interleave_classes(m1, m5);
-    const uint64_t vb = 6 * (K0 + ((uint64_t)b << logW) + c0 + lane);
-    const uint32_t q1 = 2 * lane, q5 = 2 * lane + 1;
-    if ((z >> q1) & 1ull) out[base + __popcll(z & ((1ull << q1) - 1))] = (OutT)(vb + 1);
-    if ((z >> q5) & 1ull) out[base + __popcll(z & ((1ull << q5) - 1))] = (OutT)(vb + 5);
-    base += __popcll(z);
+    const uint32_t b = u >> chunk_bits, w = ((u & cmask) << 5) + lane;
+    const uint2 x = sbuf[w];
+    const uint32_t s1 = (x.x >> b) & 1u, s5 = (x.y >> b) & 1u;
+    const uint32_t m1 = __ballot_sync(kFullMask, s1), m5 = __ballot_sync(kFullMask, s5);
+    if (s1 | s5) {
+      const uint32_t rank = __popc(m1 & lt) + __popc(m5 & lt);
+      const uint64_t v = 6 * (K0 + ((uint64_t)b << logW) + w);
+      if (s1) o[rank] = (OutT)(v + 1);
+      if (s5) o[rank + s1] = (OutT)(v + 5);
+    }
+    o += __popc(m1) + __popc(m5);
   }
 }
 

@@ -22,7 +22,9 @@ def declared_functions():
 def test_header_declares_the_calls():
     names = declared_functions()
     for must in ("sieve_create", "sieve_destroy", "sieve_count", "sieve_primes", "sieve_range",
-                 "sieve_segment_counts", "sieve_last_error"):
+                 "sieve_segment_counts", "sieve_last_error", "sieve_range_batch", "sieve_range_each",
+                 "sieve_autotune_batch", "sieve_autotune_range", "sieve_server_start", "sieve_server_submit",
+                 "sieve_server_poll", "sieve_server_next_done", "sieve_server_get_stats", "sieve_server_stop"):
         assert must in names
 
 

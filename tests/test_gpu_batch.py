@@ -196,3 +196,13 @@ def test_batch_rejects_bad_queries(sv):
     # the context still works afterwards
     cnt, _, _ = sv.range_batch([0], [100], [0])
     assert int(cnt[0][0]) == 25
+
+
+def test_batch_single_huge_tile_is_split(sv):
+    """A lone narrow query high up has one tile with millions of base primes:
+    the planner splits that tile's primes over many items (shared-memory
+    pieces ANDed in global memory)."""
+    for lo, hi, m in ((10**16 - 1000, 10**16, 1), (10**16 - 5 * 10**6, 10**16 - 4 * 10**6, 0)):
+        cnt, off, vals = sv.range_batch([lo], [hi], [m])
+        _check_against_oracle(np.array([lo], np.uint64), np.array([hi], np.uint64), np.array([m], np.uint8),
+                              cnt, off, vals)
