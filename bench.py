@@ -77,15 +77,19 @@ def small_primes(n: int):
     return np.nonzero(a)[0].astype(np.int64)
 
 
-def algorithmic_ops(lo: int, hi: int) -> dict:
-    """Work a segmented 6k+-1 sieve with a {5..19} wheel must do on [lo, hi):
-    strikes = class-1 and class-5 multiples m of each base prime 23 <= p <=
-    isqrt(hi-1) with max(lo, p^2) <= m < hi; words = candidate bits / 32, each
-    written once (presieve) and read once (count)."""
+# largest prime removed by the presieve patterns, by presieve_groups
+LAST_PRESIEVED = [19, 31, 43, 59, 71, 83, 101, 109, 131]
+
+
+def algorithmic_ops(lo: int, hi: int, first: int = 23) -> dict:
+    """Strikes a segmented 6k+-1 sieve must make on [lo, hi) once the primes
+    below `first` are presieved: class-1 and class-5 multiples m of each base
+    prime first <= p <= isqrt(hi-1) with max(lo, p^2) <= m < hi; words =
+    candidate bits / 32, each written once (presieve) and read once (count)."""
     import numpy as np
     s = math.isqrt(hi - 1)
     p = small_primes(s)
-    p = p[p >= 23]
+    p = p[p >= first]
     strikes = 0
     a = np.maximum(lo, p * p)
     jmax = (hi - 1) // p
@@ -328,7 +332,8 @@ def batch_leg(steps: int, warmup: int) -> dict:
     }
 
 
-def serving_leg(rates=(1000, 3000, 10000, 30000, 100000), seconds: float = 1.0, max_n: int = 40000) -> dict:
+def serving_leg(rates=(1000, 3000, 10000, 30000, 100000), seconds: float = 1.0, max_n: int = 40000,
+                naive_rates: int = 2) -> dict:
     """Open-loop Poisson request streams (seed 1: lo log-uniform in [1e6, 1e18],
     width in [1e3, 1e9], 20% list mode) against the continuous-batching server;
     latency = submit to result ready on the server.  Results are collected into
@@ -403,7 +408,7 @@ def serving_leg(rates=(1000, 3000, 10000, 30000, 100000), seconds: float = 1.0, 
     srv.stop()
     # one range launch per request, in arrival order, at the lowest rates
     naive = []
-    for rate in rates[:2]:
+    for rate in rates[:naive_rates]:
         n = int(min(2000, rate * seconds))
         arr = workloads.serving_arrivals(float(rate), n, seed=1)
         lat = []
@@ -510,15 +515,19 @@ def run_gpu(args):
             dist.destroy_process_group()
         return 0
 
-    # roofline of the dominant kernel (the tile sieve; one launch per step)
+    # roofline of the dominant kernel (the tile sieve; one launch per step):
+    # its strikes are shared-memory atomic ANDs, whose throughput on this
+    # device is measured live (conflict-free lanes per SM per clock)
     props = torch.cuda.get_device_properties(dev)
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0)
-    alg = algorithmic_ops(lo, hi)
-    per_launch_s = t_local / args.steps
-    achieved = alg["ops"] / per_launch_s / 1e9
-    peak = props.multi_processor_count * 32 * sm_max * 1e6 / 1e9
     opts = sv.options()
+    first = LAST_PRESIEVED[opts["presieve_groups"]] + 1
+    alg = algorithmic_ops(lo, hi, first)
+    per_launch_s = t_local / args.steps
+    atom_cf, atom_rand = binding.measure_smem_atomics(local)
+    achieved = alg["strikes"] / per_launch_s / 1e9
+    peak = props.multi_processor_count * atom_cf * sm_max * 1e6 / 1e9
     traffic = profiled_traffic("range_tiles_count_1e12.json")
 
     batch = serving = None
@@ -544,13 +553,15 @@ def run_gpu(args):
                    "group_hits": opts["group_hits"],
                    "l2": "flushed between steps (256 MiB write outside the timed events)"},
         "check": {"pi_1e12": got_count, "expected": PI_1E12, "ok": got_count == PI_1E12},
-        "roofline": {"bound": "alu", "resource": "SM shared-memory read-modify-write lane ops "
-                                                  "(one 32-lane shared access per SM per clock)",
+        "roofline": {"bound": "alu", "resource": "shared-memory atomic AND lane operations (the strikes)",
                      "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
                      "traffic": traffic, "kernel": "range_tiles_kernel",
-                     "ops_per_launch": alg["ops"], "strikes_per_launch": alg["strikes"],
-                     "peak_basis": f"{props.multi_processor_count} SMs x 32 lanes x {sm_max:.0f} MHz "
-                                   f"({'measured' if peaks else 'fallback'} max SM clock)"},
+                     "strikes_per_launch": alg["strikes"], "candidate_words_per_launch": alg["candidate_words"],
+                     "peak_basis": f"measured (sieve_measure_smem_atomics, live): {atom_cf:.2f} conflict-free "
+                                   f"lane-ops/clk/SM ({atom_rand:.2f} at random banks) x "
+                                   f"{props.multi_processor_count} SMs x {sm_max:.0f} MHz "
+                                   f"({'measured' if peaks else 'fallback'} max SM clock)",
+                     "peak_nominal_smem": props.multi_processor_count * 32 * sm_max * 1e6 / 1e9},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16,
                 "d2h_bytes_per_step": 8 * nb + 16},

@@ -312,6 +312,18 @@ void sieve_server_stop(sieve_server *srv);
 int sieve_range_list_noalloc(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *out, size_t cap,
                              size_t *n_out, sieve_count_result *cnt);
 
+/* ------------------------------------------------------------- measurement */
+
+/* The paper has no counterpart to this call; it measures the device resource
+ * that bounds the strike loops, for roofline reporting: the throughput of
+ * 32-bit shared-memory atomic AND, in lane operations per SM per clock, with
+ * one CTA of 1024 threads per SM issuing 4096 atomics per thread into 128 KB
+ * of shared memory -- conflict-free (lane l always on bank l) and at
+ * pseudo-random words.  Times the slowest SM with clock64, so the result does
+ * not depend on the clock.  Runs on the legacy default stream of `device`
+ * and synchronises it.  Errors: INVALID, CUDA, OOM. */
+int sieve_measure_smem_atomics(int device, double *conflict_free, double *random_banks);
+
 /* ------------------------------------------------------------- table 1 */
 
 /* Host evaluation of the start-index routine the kernels run (Section 3,

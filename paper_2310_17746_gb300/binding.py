@@ -110,6 +110,7 @@ SIGNATURES = {
     "sieve_server_next_done": (_i, [_p, ctypes.POINTER(_u64), _i]),
     "sieve_server_get_stats": (_i, [_p, ctypes.POINTER(ServerStats), _i]),
     "sieve_server_stop": (None, [_p]),
+    "sieve_measure_smem_atomics": (_i, [_i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
 }
 
 
@@ -141,6 +142,16 @@ def table1_start(B: int, M: int, P: int) -> tuple[int, int]:
     a = ctypes.c_int64(0)
     b = ctypes.c_int64(0)
     _check(lib().sieve_table1_start(B, M, P, ctypes.byref(a), ctypes.byref(b)), "sieve_table1_start")
+    return a.value, b.value
+
+
+def measure_smem_atomics(device: int = 0) -> tuple[float, float]:
+    """(conflict-free, random-bank) shared-memory atomic AND throughput of the
+    device, in lane operations per SM per clock."""
+    a = ctypes.c_double(0.0)
+    b = ctypes.c_double(0.0)
+    _check(lib().sieve_measure_smem_atomics(int(device), ctypes.byref(a), ctypes.byref(b)),
+           "sieve_measure_smem_atomics")
     return a.value, b.value
 
 

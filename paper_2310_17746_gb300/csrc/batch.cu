@@ -49,16 +49,20 @@ __device__ __forceinline__ void emit_tile(const BatchArena &a, const BatchQuery 
                                           uint64_t K0, uint64_t *red) {
   const bool list = (qd.flags & kQueryList) != 0;
   uint2 *bm = list ? a.list_bm + qd.bitmap_off + (uint64_t)t * W : nullptr;
-  uint64_t cnt = 0, sum = 0, unused = 0;
+  // 32-bit per-thread sums (as in the range kernel): class counts, the
+  // word-weighted count and the bit-position sum; the 64-bit checksum once
+  uint32_t c1 = 0, c5 = 0, sw = 0, bs = 0;
   for (uint32_t w = threadIdx.x; w < W; w += BLOCK) {
     const uint32_t x = s1[w], y = s5[w];
     if (list) bm[w] = make_uint2(x, y);
     const uint32_t cx = __popc(x), cy = __popc(y);
-    cnt += cx + cy;
-    const uint64_t vb = 6 * (K0 + w);
-    sum += (uint64_t)cx * (vb + 1) + (uint64_t)cy * (vb + 5) +
-           6ull * W * (uint64_t)(bit_index_sum(x) + bit_index_sum(y));
+    c1 += cx;
+    c5 += cy;
+    sw += w * (cx + cy);
+    bs += bit_index_sum(x) + bit_index_sum(y);
   }
+  uint64_t cnt = (uint64_t)c1 + c5, unused = 0;
+  uint64_t sum = (uint64_t)c1 * (6 * K0 + 1) + (uint64_t)c5 * (6 * K0 + 5) + 6ull * sw + 6ull * W * bs;
   block_sum3<BLOCK>(cnt, sum, unused, red);
   if (threadIdx.x == 0) {
     if (K0 == 0) {  // 2 and 3 are outside the residue arrays (Section 2.1)

@@ -101,21 +101,26 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
 
     // popcount, checksum, and the count below the segment boundary (if any).
     // Word w holds indices w + b W: their values sum to
-    // popc * (6 (K0 + w) + r) + 6 W * (sum of the set bit positions b).
-    uint64_t cnt = 0, sum = 0, below = 0;
+    // popc * (6 (K0 + w) + r) + 6 w popc + 6 W * (sum of the set bit positions b),
+    // so a thread accumulates, in 32 bits, the class counts c1 / c5, the
+    // word-weighted count sw and the bit-position sum bs of its words
+    // (sw < 2^15 * 64 * (W / BLOCK) < 2^32), and forms the 64-bit sum once.
+    uint32_t c1 = 0, c5 = 0, sw = 0, bs = 0, below32 = 0;
     const int has_b = sh_has_boundary;
     const int64_t t1 = has_b ? sh_t1 : 0, t5 = has_b ? sh_t5 : 0;
     for (uint32_t w = threadIdx.x; w < W; w += BLOCK) {
       const uint32_t a = s1[w], b = s5[w];
       if (LIST) p.bitmap[(uint64_t)t * W + w] = make_uint2(a, b);
       const uint32_t ca = __popc(a), cb = __popc(b);
-      cnt += ca + cb;
-      const uint64_t vb = 6 * (K0 + w);
-      sum += (uint64_t)ca * (vb + 1) + (uint64_t)cb * (vb + 5) +
-             6ull * W * (uint64_t)(bit_index_sum(a) + bit_index_sum(b));
+      c1 += ca;
+      c5 += cb;
+      sw += w * (ca + cb);
+      bs += bit_index_sum(a) + bit_index_sum(b);
       if (has_b)
-        below += __popc(a & below_mask(t1, w, tg.logW, W)) + __popc(b & below_mask(t5, w, tg.logW, W));
+        below32 += __popc(a & below_mask(t1, w, tg.logW, W)) + __popc(b & below_mask(t5, w, tg.logW, W));
     }
+    uint64_t cnt = (uint64_t)c1 + c5, below = below32;
+    uint64_t sum = (uint64_t)c1 * (6 * K0 + 1) + (uint64_t)c5 * (6 * K0 + 5) + 6ull * sw + 6ull * W * bs;
     block_sum3<BLOCK>(cnt, sum, below, red);
     if (threadIdx.x == 0) {
       if (K0 == 0) {  // 2 and 3 are outside the residue arrays (Section 2.1)

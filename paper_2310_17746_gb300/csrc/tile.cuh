@@ -170,8 +170,12 @@ __device__ __forceinline__ void strike_primes(uint32_t *s1, uint32_t *s5, uint64
     }
     uint64_t k1, k5;
     if (tile_starts_within(B, P, m, span6, k1, k5)) {
-      if (k1 < len) strike(s1, (uint32_t)k1, P, len, wmask, logW);
-      if (k5 < len) strike(s5, (uint32_t)k5, P, len, wmask, logW);
+      // a plain loop per class: lane-band primes have few hits per tile, so
+      // the unrolled loop's set-up costs more than it saves (measured)
+      if (k1 < len)  // k1, k5 may exceed 2^32 on the general path; k + P < 2^32 (P < 2^31.6)
+        for (uint32_t k = (uint32_t)k1; k < len; k += P) strike_one(s1, k, wmask, logW);
+      if (k5 < len)
+        for (uint32_t k = (uint32_t)k5; k < len; k += P) strike_one(s5, k, wmask, logW);
     }
     i = in;
     P = Pn;
