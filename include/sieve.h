@@ -162,6 +162,18 @@ int sieve_segment_counts(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t seg_
                          uint64_t *counts, size_t ncounts, sieve_count_result *total,
                          unsigned flags);
 
+/* The first k primes greater than `after`, increasing, into out[0..k) (host
+ * memory, or device memory with SIEVE_OUT_DEVICE); *n_out = k on success.
+ * Incremental in the paper's sense (Sections 2.4 and 4): no upper bound is
+ * fixed in advance -- the call sieves forward in windows and, when a window
+ * reaches past the square of the base table's limit, grows the table with
+ * the sieve itself (the new primes come from sieving the table's extension
+ * with the current table).  A chain of calls, each starting after the last
+ * prime of the previous one, streams the primes without end (up to 2^63).
+ * Growing the table moves it: device pointers from sieve_base_table become
+ * stale.  Errors: INVALID, RANGE (past 2^63), OOM, CUDA. */
+int sieve_next(sieve_ctx *ctx, uint64_t after, size_t k, uint64_t *out, size_t *n_out, unsigned flags);
+
 /* ------------------------------------------------------------- batches */
 
 /* Many independent ranges in one call: query i is [lo[i], hi[i]) in mode

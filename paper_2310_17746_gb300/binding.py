@@ -111,6 +111,7 @@ SIGNATURES = {
     "sieve_server_get_stats": (_i, [_p, ctypes.POINTER(ServerStats), _i]),
     "sieve_server_stop": (None, [_p]),
     "sieve_measure_smem_atomics": (_i, [_i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "sieve_next": (_i, [_p, _u64, _sz, _p, ctypes.POINTER(_sz), _u]),
 }
 
 
@@ -303,6 +304,22 @@ class Sieve:
         nout = _sz(0)
         _check(self._lib.sieve_range(self._h, int(lo), int(hi), LIST, None, ptr, cap, ctypes.byref(nout), flags),
                "sieve_range")
+        return int(nout.value)
+
+    def next_primes(self, after: int, k: int, out=None):
+        """The first k primes greater than `after` (incremental: the base
+        table grows as needed).  Into `out` (numpy uint64 or torch CUDA int64;
+        returns the number written) or a new numpy array."""
+        if out is None:
+            out = np.empty(max(int(k), 1), dtype=np.uint64)
+            n = self.next_primes(after, k, out)
+            return out[:n]
+        ptr, flags = _ptr_and_flag(out)
+        cap = out.numel() if _is_torch_cuda(out) else out.size
+        if k > cap:
+            raise ValueError("out holds fewer than k elements")
+        nout = _sz(0)
+        _check(self._lib.sieve_next(self._h, int(after), int(k), ptr, ctypes.byref(nout), flags), "sieve_next")
         return int(nout.value)
 
     def range_list_noalloc(self, lo: int, hi: int, out) -> tuple[int, CountAndSum]:

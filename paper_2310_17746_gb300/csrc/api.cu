@@ -319,6 +319,86 @@ static int build_base_table(sieve_ctx *c, uint64_t limit) {
   return SIEVE_OK;
 }
 
+namespace sieve {
+
+// Grow the base table to every prime <= new_limit (Section 2.4: the sieving
+// primes are found incrementally -- the current table, complete up to L,
+// sieves (L, new_limit] as long as new_limit <= L^2).  The table moves to new
+// device arrays; kernels launched earlier have completed (the stream is
+// synchronised first) and batch runners notice the new table epoch.
+int extend_base_table(sieve_ctx *c, uint64_t new_limit) {
+  const uint64_t L = c->table.limit;
+  if (new_limit <= L) return SIEVE_OK;
+  if (new_limit > L * L) new_limit = L * L;
+  if (new_limit > 0xFFFFFFFFull) new_limit = 0xFFFFFFFFull;
+  const uint64_t cap = pi_upper(new_limit);
+  uint32_t *np_ = nullptr;
+  uint64_t *nm = nullptr;
+  SIEVE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  SIEVE_CUDA_TRY(cudaMalloc(&np_, cap * sizeof(uint32_t)));
+  cudaError_t e = cudaMalloc(&nm, cap * sizeof(uint64_t));
+  if (e != cudaSuccess) {
+    cudaFree(np_);
+    return cuda_fail(e, "cudaMalloc (base table)");
+  }
+  const uint32_t n0 = c->table.nprimes;
+  int rc = SIEVE_OK;
+  size_t n = 0;
+  do {
+    if ((e = cudaMemcpyAsync(np_, c->d_primes, n0 * sizeof(uint32_t), cudaMemcpyDeviceToDevice, c->stream)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(nm, c->d_magic, n0 * sizeof(uint64_t), cudaMemcpyDeviceToDevice, c->stream)) !=
+            cudaSuccess) {
+      rc = cuda_fail(e, "cudaMemcpyAsync (base table)");
+      break;
+    }
+    RangeRequest rq;
+    rq.lo = L + 1;
+    rq.hi = new_limit + 1;
+    rq.list = 1;
+    rq.out_bytes = 4;
+    rq.out = np_ + n0;
+    rq.cap = cap - n0;
+    rq.out_on_device = 1;
+    if ((rc = run_range(c, c->table, rq, &n)) != SIEVE_OK) break;
+    if (n) {
+      reciprocal_kernel<<<(uint32_t)((n + 255) / 256), 256, 0, c->stream>>>(np_ + n0, nm + n0, (uint32_t)n);
+      c->launches++;
+      if ((e = cudaGetLastError()) != cudaSuccess) {
+        rc = cuda_fail(e, "reciprocal_kernel");
+        break;
+      }
+    }
+    c->h_primes.resize(n0 + n);
+    if ((e = cudaMemcpyAsync(c->h_primes.data() + n0, np_ + n0, n * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                             c->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess) {
+      rc = cuda_fail(e, "base table read-back");
+      break;
+    }
+  } while (0);
+  if (rc != SIEVE_OK) {
+    c->h_primes.resize(n0);
+    cudaFree(np_);
+    cudaFree(nm);
+    return rc;
+  }
+  cudaFree(c->d_primes);
+  cudaFree(c->d_magic);
+  c->d_primes = np_;
+  c->d_magic = nm;
+  c->table.primes = np_;
+  c->table.magic = nm;
+  c->table.host_primes = c->h_primes.data();
+  c->table.nprimes = (uint32_t)(n0 + n);
+  c->table.limit = new_limit;
+  c->max_hi = new_limit >= 0xB504F333ull ? (1ull << 63) : (new_limit + 1) * (new_limit + 1);
+  c->table_epoch++;
+  return SIEVE_OK;
+}
+
+}  // namespace sieve
+
 extern "C" int sieve_create(sieve_ctx **ctx, uint64_t max_hi, int device, void *cuda_stream) {
   if (!ctx) {
     set_error("ctx is NULL");

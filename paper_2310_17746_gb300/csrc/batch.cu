@@ -32,13 +32,41 @@ __global__ void batch_init_kernel(const BatchArena a) {
   for (uint64_t i = tid; i < words / 4; i += nth) bm4[i] = ones;
 }
 
+// L2 cache policies (PTX createpolicy): strips stream the base table once per
+// query, which would push the query's bitmap -- the target of their atomics --
+// out of L2.  Table loads are marked evict-first and the atomics evict-last.
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint32_t ld_hint_u32(const uint32_t *a, uint64_t pol) {
+  uint32_t v;
+  asm volatile("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint64_t ld_hint_u64(const uint64_t *a, uint64_t pol) {
+  uint64_t v;
+  asm volatile("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void red_and_hint(uint32_t *a, uint32_t v, uint64_t pol) {
+  asm volatile("red.global.and.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(a), "r"(v), "l"(pol) : "memory");
+}
+
 // Clear index k (query-relative) of class c in a merged query's bitmap: tile
 // k >> logL, in-tile index kk, word kk mod W of that class, bit kk div W.
-__device__ __forceinline__ void strike_merged(uint32_t *gq, uint64_t k, uint32_t c, uint32_t logL, uint32_t logW) {
+__device__ __forceinline__ void strike_merged(uint32_t *gq, uint64_t k, uint32_t c, uint32_t logL, uint32_t logW,
+                                              uint64_t pol) {
   const uint64_t t = k >> logL;
   const uint32_t kk = (uint32_t)k & ((1u << logL) - 1u);
   const uint32_t W = 1u << logW;
-  atomicAnd(gq + t * 2ull * W + (uint64_t)c * W + (kk & (W - 1u)), rotl32(0xFFFFFFFEu, kk >> logW));
+  red_and_hint(gq + t * 2ull * W + (uint64_t)c * W + (kk & (W - 1u)), rotl32(0xFFFFFFFEu, kk >> logW), pol);
 }
 
 // Count / checksum a finished tile held in s1 / s5 (fix-ups applied), write
@@ -115,12 +143,13 @@ __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK > 0 ? 1024 / BLOCK : 1)) 
       const uint64_t Bq = 6 * qd.k_begin;
       const uint64_t span = qd.k_end - qd.k_begin;
       uint32_t *gq = a.slot_bm + qd.slot_base;
+      const uint64_t stream = l2_policy_evict_first(), keep = l2_policy_evict_last();
       for (uint32_t i = it.i0 + threadIdx.x; i < it.i1; i += BLOCK) {
-        const uint32_t P = __ldg(a.primes + i);
+        const uint32_t P = ld_hint_u32(a.primes + i, stream);
         uint64_t k1, k5;
-        tile_starts(Bq, P, __ldg(a.magic + i), k1, k5);
-        for (uint64_t k = k1; k < span; k += P) strike_merged(gq, k, 0, logL, logW);
-        for (uint64_t k = k5; k < span; k += P) strike_merged(gq, k, 1, logL, logW);
+        tile_starts(Bq, P, ld_hint_u64(a.magic + i, stream), k1, k5);
+        for (uint64_t k = k1; k < span; k += P) strike_merged(gq, k, 0, logL, logW, keep);
+        for (uint64_t k = k5; k < span; k += P) strike_merged(gq, k, 1, logL, logW, keep);
       }
       __syncthreads();
       continue;
@@ -156,10 +185,11 @@ __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK > 0 ? 1024 / BLOCK : 1)) 
     if (merged) {
       // AND the shared-memory result into the query's bitmap in global memory
       uint32_t *g1 = a.slot_bm + qd.slot_base + (uint64_t)it.t * 2 * W, *g5 = g1 + W;
+      const uint64_t keep = l2_policy_evict_last();
       for (uint32_t w = threadIdx.x; w < W; w += BLOCK) {
         const uint32_t x = s1[w], y = s5[w];
-        if (x != 0xFFFFFFFFu) atomicAnd(g1 + w, x);
-        if (y != 0xFFFFFFFFu) atomicAnd(g5 + w, y);
+        if (x != 0xFFFFFFFFu) red_and_hint(g1 + w, x, keep);
+        if (y != 0xFFFFFFFFu) red_and_hint(g5 + w, y, keep);
       }
     } else {
       fixup_tile<BLOCK>(s1, s5, tg, K0, valid_range(qd.lo, qd.hi, B, tg.len), npat);
@@ -397,7 +427,9 @@ int configure(BatchRunner &r) {
     return SIEVE_ERR_INVALID;
   }
   const size_t fsmem = (size_t)(Lmax / 32) * 2 * sizeof(uint32_t);
-  if (r.exec && threads == r.threads && logLmax == r.logLmax && band == r.band_max) return SIEVE_OK;
+  if (r.exec && threads == r.threads && logLmax == r.logLmax && band == r.band_max &&
+      r.table_epoch == ctx->table_epoch)
+    return SIEVE_OK;
   void *fn = sieve_kernel_fn(threads);
   SIEVE_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->smem_optin));
   SIEVE_CUDA_TRY(cudaFuncSetAttribute((void *)batch_finish_kernel<kFinishThreads>,
@@ -476,6 +508,7 @@ int build_graph(BatchRunner &r) {
   SIEVE_CUDA_TRY(cudaGraphAddKernelNode(&n_compact, g, &n_scan, 1, &kp));
   SIEVE_CUDA_TRY(cudaGraphInstantiate(&r.exec, g, 0));
   r.n_copy = n_copy;
+  r.table_epoch = r.ctx->table_epoch;
   return SIEVE_OK;
 }
 
@@ -500,7 +533,8 @@ double lnln(double x) { return std::log(std::log(std::max(x, 23.0))); }
 constexpr double kCostItem = 4000.0;   // fixed per item: barriers, set-up
 constexpr double kCostPrime = 10.0;    // one Table 1 evaluation
 constexpr double kCostWord = 6.0;      // presieve copy + count of one word pair
-constexpr double kCostGlobal = 40.0;   // one atomic AND in global memory (L2-resident bitmap)
+constexpr double kCostGlobal = 75.0;   // one atomic AND in global memory (L2-resident bitmap):
+                                       // measured ~7.5x a Table 1 evaluation on GB300
 constexpr double kL2Bitmap = 48e6;     // a merged query's bitmap above this many bytes
                                        // spills from L2: its atomics cost 4x
 constexpr uint32_t kMinChunk = 256;    // fewest primes in a split piece of a tile

@@ -132,6 +132,7 @@ struct BatchRunner {
   size_t plan_bytes = 0;
   uint32_t used_logW = 0;  // bit mask of tile widths in the plan
   uint32_t batch_id = 0;   // id of the last planned batch (first is 1)
+  uint32_t table_epoch = 0;  // base-table epoch the graph's kernel arguments point into
 };
 
 // Runner operations (batch.cu).

@@ -263,6 +263,7 @@ struct sieve_ctx {
   } sliced[32];
   sieve_options opt{};
   std::atomic<uint64_t> launches{0};  // read by other threads while a server runs
+  uint32_t table_epoch = 0;           // bumped whenever the base table moves
   // device copy of the pattern sets, indexed by log2(W); entry i is valid
   // when bit i of psets_ready is set
   sieve::PatternSetDev *d_psets = nullptr;
@@ -309,6 +310,10 @@ int range_set_smem_attributes(int bytes);
 int sliced_patterns(sieve_ctx *ctx, uint32_t logW, const uint32_t **ptr, PatternDesc *pd);
 // Make sure the device table entry for log2(W) = logW is filled (api.cu).
 int ensure_pattern_set_dev(sieve_ctx *ctx, uint32_t logW);
+
+// Grow the base table to every prime <= new_limit (at most the square of
+// its current limit; api.cu).
+int extend_base_table(sieve_ctx *ctx, uint64_t new_limit);
 
 // batch runner lifetime (batch.cu)
 void destroy_batch_runner(BatchRunner *r);
