@@ -533,8 +533,8 @@ double lnln(double x) { return std::log(std::log(std::max(x, 23.0))); }
 constexpr double kCostItem = 4000.0;   // fixed per item: barriers, set-up
 constexpr double kCostPrime = 10.0;    // one Table 1 evaluation
 constexpr double kCostWord = 6.0;      // presieve copy + count of one word pair
-constexpr double kCostGlobal = 75.0;   // one atomic AND in global memory (L2-resident bitmap):
-                                       // measured ~7.5x a Table 1 evaluation on GB300
+constexpr double kCostGlobal = 40.0;   // one atomic AND in global memory (L2-resident bitmap);
+                                       // 75 measured slower on the batch and serving mixes
 constexpr double kL2Bitmap = 48e6;     // a merged query's bitmap above this many bytes
                                        // spills from L2: its atomics cost 4x
 constexpr uint32_t kMinChunk = 256;    // fewest primes in a split piece of a tile
