@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(BLOCK) batch_scan_kernel(const BatchArena a) {
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) batch_compact_kernel(const BatchArena a) {
   constexpr int NWARPS = BLOCK / 32;
-  __shared__ uint64_t warp_base[NWARPS];
+  __shared__ uint32_t warp_cnt[NWARPS * 32];
   extern __shared__ __align__(16) uint2 sbuf[];  // one tile's bitmap (up to Wmax pairs)
   const char *plan = (const char *)a.plan;
   const BatchHeader *hdr = (const BatchHeader *)plan;
@@ -319,10 +319,6 @@ __global__ void __launch_bounds__(BLOCK) batch_compact_kernel(const BatchArena a
       off = qd.out_base + (off - q0);
     }
     const uint64_t K0 = qd.k_begin + (uint64_t)qt.y * L;
-    const uint64_t left = qd.k_end - K0;
-    const uint32_t len = left < L ? (uint32_t)left : L;
-    const uint32_t chunk_bits = logW - 5;
-    const uint32_t units = ((len + W - 1) >> logW) << chunk_bits;
     if (K0 == 0) {  // 2 and 3 first
       const uint32_t e2 = (qd.lo <= 2 && 2 < qd.hi), e3 = (qd.lo <= 3 && 3 < qd.hi);
       if (threadIdx.x == 0) {
@@ -332,8 +328,8 @@ __global__ void __launch_bounds__(BLOCK) batch_compact_kernel(const BatchArena a
       }
       off += e2 + e3;
     }
-    compact_tile<BLOCK, uint64_t>(a.list_bm + qd.bitmap_off + (uint64_t)qt.y * W, logW, units, chunk_bits, K0, off,
-                                  out, warp_base, sbuf);
+    compact_tile<BLOCK, uint64_t>(a.list_bm + qd.bitmap_off + (uint64_t)qt.y * W, logW, K0, off, out, warp_cnt,
+                                  sbuf);
     __syncthreads();
   }
 }
@@ -735,25 +731,27 @@ int batch_plan(BatchRunner &r, const uint64_t *lo, const uint64_t *hi, const uin
     return SIEVE_ERR_INVALID;
   }
 
-  // cost order (largest first) by a counting sort on log2 buckets: items
-  // that cost more start earlier, so the queue drains evenly (longest
-  // processing time first).  The items of a merged query share one key (the
-  // query's total), so they run together and its bitmap in global memory
-  // stays in L2 while it is struck.
+  // Order: first the merged queries, one query's items after another
+  // (largest query first), so that all CTAs strike one query's bitmap in
+  // global memory at a time and it stays in L2; then the single-tile items,
+  // largest first, so that the queue drains evenly (longest processing time
+  // first).  A counting sort on log2 buckets of the cost, stable, so a
+  // query's items stay together.
   const size_t ni = r.items.size();
   for (size_t j = 0; j < ni; j++) info[r.items[j].q].total += r.cost[j];
   constexpr int kBuckets = 128;
-  size_t bucket_n[kBuckets + 1] = {0};
+  size_t bucket_n[2 * kBuckets + 1] = {0};
   std::vector<uint8_t> bk(ni);
   for (size_t j = 0; j < ni; j++) {
     const uint32_t qj = r.items[j].q;
-    const float key = (r.q[qj].flags & kQueryMerged) ? (float)info[qj].total : r.cost[j];
+    const bool merged = (r.q[qj].flags & kQueryMerged) != 0;
+    const float key = merged ? (float)info[qj].total : r.cost[j];
     int b = (int)(4.0f * std::log2(std::max(key, 1.0f)));
     b = std::min(std::max(b, 0), kBuckets - 1);
-    bk[j] = (uint8_t)(kBuckets - 1 - b);
+    bk[j] = (uint8_t)((merged ? 0 : kBuckets) + kBuckets - 1 - b);
     bucket_n[bk[j] + 1]++;
   }
-  for (int b = 0; b < kBuckets; b++) bucket_n[b + 1] += bucket_n[b];
+  for (int b = 0; b < 2 * kBuckets; b++) bucket_n[b + 1] += bucket_n[b];
   r.sorted.resize(ni);
   for (size_t j = 0; j < ni; j++) r.sorted[bucket_n[bk[j]]++] = r.items[j];
 

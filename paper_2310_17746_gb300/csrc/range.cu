@@ -202,18 +202,13 @@ struct CompactParams {
 template <int BLOCK, typename OutT>
 __global__ void __launch_bounds__(BLOCK) compact_kernel(const CompactParams p) {
   constexpr int NWARPS = BLOCK / 32;
-  __shared__ uint64_t warp_base[NWARPS];
+  __shared__ uint32_t warp_cnt[NWARPS * 32];
   extern __shared__ __align__(16) uint2 sbuf[];  // one tile's bitmap (W pairs)
   if (p.offsets[p.ntiles] > p.cap) return;  // capacity: the host reports it
   OutT *out = (OutT *)p.out;
   const uint32_t W = p.L / 32;
-  const uint32_t chunk_bits = p.logW - 5;  // chunks per row = W / 32
   for (uint32_t t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
     const uint64_t K0 = p.k_begin + (uint64_t)t * p.L;
-    const uint64_t left = p.k_end - K0;
-    const uint32_t len = left < p.L ? (uint32_t)left : p.L;
-    const uint32_t rows = (len + W - 1) >> p.logW;
-    const uint32_t units = rows << chunk_bits;
     const uint2 *bm = p.bitmap + (uint64_t)t * W;
     uint64_t off = p.offsets[t];
     if (K0 == 0) {  // 2 and 3 first
@@ -224,7 +219,7 @@ __global__ void __launch_bounds__(BLOCK) compact_kernel(const CompactParams p) {
       }
       off += (p.lo <= 2 && 2 < p.hi) + (p.lo <= 3 && 3 < p.hi);
     }
-    compact_tile<BLOCK, OutT>(bm, p.logW, units, chunk_bits, K0, off, out, warp_base, sbuf);
+    compact_tile<BLOCK, OutT>(bm, p.logW, K0, off, out, warp_cnt, sbuf);
     __syncthreads();
   }
 }

@@ -283,69 +283,96 @@ __device__ __forceinline__ void block_sum3(uint64_t &a, uint64_t &b, uint64_t &c
   }
 }
 
+// 32 x 32 bit transpose across a warp: on return, bit j of lane i's word is
+// bit i of lane j's input word.  Five exchange stages; at stage s a lane
+// keeps the half of each 2s-bit block that stays on its side and takes the
+// other half from lane ^ s.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, uint32_t lane) {
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    const uint32_t m = s == 16 ? 0x0000FFFFu : s == 8 ? 0x00FF00FFu : s == 4 ? 0x0F0F0F0Fu : s == 2 ? 0x33333333u
+                                                                                                   : 0x55555555u;
+    const uint32_t y = __shfl_xor_sync(kFullMask, x, s);
+    x = (lane & s) ? ((x & ~m) | ((y & ~m) >> s)) : ((x & m) | ((y & m) << s));
+  }
+  return x;
+}
+
 // Write the survivors of one tile, in value order, to out[off, ...).  The
 // tile's bitmap bm holds W = 2^logW (class-1 word, class-5 word) pairs in the
-// sliced layout.  Row b of the tile is the index run [b W, b W + W); a unit
-// (b, c) is the 32 indices b W + 32 c + j, j = 0..31, and units in row-major
-// order are in value order.  In a unit, lane j reads word 32 c + j, so its
-// own candidates are bit b of its two words: the values 6 k + 1 and 6 k + 5
-// with k = K0 + b W + 32 c + j.  Their rank among the unit's survivors (value
-// order 6k+1 < 6k+5 < 6(k+1)+1) is the number of survivors of lower lanes in
-// both classes -- two ballots and two popcounts -- plus 1 for the 6k+5 value
-// when 6k+1 survives.  Each warp owns a contiguous run of units; a first pass
-// counts them and a block scan (in warp_base, NWARPS entries) places the
-// warps.  The bitmap is first staged in shared memory (sbuf, W entries, with
-// 16-byte loads; bm must be 16-byte aligned) so that both passes read it at
-// shared-memory latency.  Bits outside the valid range must already be clear.
+// sliced layout: index k = b W + w is bit b of word w, so row b (bit b of
+// every word) is the index run [b W, b W + W), and value order is row-major.
+// The bitmap is staged in shared memory (sbuf, W pairs; bm 16-byte aligned).
+// Warp g takes the word chunks [g C / NWARPS, (g+1) C / NWARPS) of every row
+// (C = W / 32).  For a chunk, each lane loads one word pair and the warp
+// transposes the two 32 x 32 bit blocks, after which lane b holds row b's 32
+// candidates of each class for that chunk.  Pass 1: each lane counts its
+// row's survivors over the warp's chunks (warp_cnt[g][b], NWARPS x 32
+// entries), and the offsets follow from a row-major prefix sum.  Pass 2
+// writes the values (below).  Bits outside the valid range must already be
+// clear.
 template <int BLOCK, typename OutT>
-__device__ __forceinline__ void compact_tile(const uint2 *__restrict__ bm, uint32_t logW, uint32_t units,
-                                             uint32_t chunk_bits, uint64_t K0, uint64_t off, OutT *out,
-                                             uint64_t *warp_base, uint2 *sbuf) {
+__device__ __forceinline__ void compact_tile(const uint2 *__restrict__ bm, uint32_t logW, uint64_t K0, uint64_t off,
+                                             OutT *out, uint32_t *warp_cnt, uint2 *sbuf) {
   constexpr int NWARPS = BLOCK / 32;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t W = 1u << logW, C = W / 32;
   {
     const uint4 *src = (const uint4 *)bm;
     uint4 *dst = (uint4 *)sbuf;
-    for (uint32_t i = threadIdx.x; i < (1u << logW) / 2; i += BLOCK) dst[i] = __ldg(src + i);
+    for (uint32_t i = threadIdx.x; i < W / 2; i += BLOCK) dst[i] = __ldg(src + i);
   }
   __syncthreads();
-  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t lt = (1u << lane) - 1u;  // lanes below this one
-  const uint32_t cmask = (1u << chunk_bits) - 1u;
-  const uint32_t per_warp = (units + NWARPS - 1) / NWARPS;
-  const uint32_t u_begin = min(warp * per_warp, units);
-  const uint32_t u_end = min(u_begin + per_warp, units);
-  uint32_t c = 0;
-  for (uint32_t u = u_begin; u < u_end; u++) {
-    const uint32_t b = u >> chunk_bits;
-    const uint2 x = sbuf[((u & cmask) << 5) + lane];
-    c += ((x.x >> b) & 1u) + ((x.y >> b) & 1u);
+  const uint32_t c_begin = (uint32_t)((uint64_t)warp * C / NWARPS);
+  const uint32_t c_end = (uint32_t)((uint64_t)(warp + 1) * C / NWARPS);
+  uint32_t cnt = 0;
+  for (uint32_t c = c_begin; c < c_end; c++) {
+    const uint2 x = sbuf[(c << 5) + lane];
+    cnt += __popc(warp_transpose32(x.x, lane)) + __popc(warp_transpose32(x.y, lane));
   }
+  warp_cnt[warp * 32 + lane] = cnt;
+  __syncthreads();
+  if (warp == 0) {  // row-major prefix: rows in order, within a row the warps in order
+    uint32_t row = 0;
+    for (int g = 0; g < NWARPS; g++) row += warp_cnt[g * 32 + lane];
+    uint32_t incl = row;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFullMask, c, o);
-  if (lane == 0) warp_base[warp] = c;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint64_t run = off;
-    for (int i = 0; i < NWARPS; i++) {
-      const uint64_t ci = warp_base[i];
-      warp_base[i] = run;
-      run += ci;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFullMask, incl, o);
+      if (lane >= (uint32_t)o) incl += y;
+    }
+    uint32_t run = incl - row;
+    for (int g = 0; g < NWARPS; g++) {
+      const uint32_t cg = warp_cnt[g * 32 + lane];
+      warp_cnt[g * 32 + lane] = run;
+      run += cg;
     }
   }
   __syncthreads();
-  OutT *o = out + warp_base[warp];
-  for (uint32_t u = u_begin; u < u_end; u++) {
-    const uint32_t b = u >> chunk_bits, w = ((u & cmask) << 5) + lane;
-    const uint2 x = sbuf[w];
-    const uint32_t s1 = (x.x >> b) & 1u, s5 = (x.y >> b) & 1u;
-    const uint32_t m1 = __ballot_sync(kFullMask, s1), m5 = __ballot_sync(kFullMask, s5);
-    if (s1 | s5) {
-      const uint32_t rank = __popc(m1 & lt) + __popc(m5 & lt);
-      const uint64_t v = 6 * (K0 + ((uint64_t)b << logW) + w);
-      if (s1) o[rank] = (OutT)(v + 1);
-      if (s5) o[rank + s1] = (OutT)(v + 5);
+  // Pass 2, chunk by chunk: lane b keeps row b's running output position;
+  // for each row the warp receives the row's two masks and position by
+  // shuffles, and lane j writes the values of its own index -- consecutive
+  // lanes, consecutive outputs, so the stores coalesce.
+  uint32_t pos = warp_cnt[warp * 32 + lane];
+  const uint32_t lt = (1u << lane) - 1u;  // lanes below this one
+  const uint64_t v0 = 6 * K0;
+  for (uint32_t c = c_begin; c < c_end; c++) {
+    const uint2 x = sbuf[(c << 5) + lane];
+    const uint32_t t1 = warp_transpose32(x.x, lane), t5 = warp_transpose32(x.y, lane);
+    const uint32_t row_n = __popc(t1) + __popc(t5);
+#pragma unroll 4
+    for (uint32_t b = 0; b < 32; b++) {
+      const uint32_t m1 = __shfl_sync(kFullMask, t1, b), m5 = __shfl_sync(kFullMask, t5, b);
+      const uint32_t base = __shfl_sync(kFullMask, pos, b);
+      const uint32_t s1 = (m1 >> lane) & 1u, s5 = (m5 >> lane) & 1u;
+      if (s1 | s5) {
+        OutT *o = out + off + base + __popc(m1 & lt) + __popc(m5 & lt);
+        const uint64_t v = v0 + 6ull * ((b << logW) + (c << 5) + lane);
+        if (s1) *o++ = (OutT)(v + 1);
+        if (s5) *o = (OutT)(v + 5);
+      }
     }
-    o += __popc(m1) + __popc(m5);
+    pos += row_n;
   }
 }
 
