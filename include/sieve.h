@@ -148,7 +148,12 @@ int sieve_primes_u32(sieve_ctx *ctx, uint64_t n, uint32_t *out, size_t cap, size
 /* Primes in [lo, hi).  mode SIEVE_COUNT fills *cnt; mode SIEVE_LIST also
  * writes the primes to out[0..cap) as uint64 with the CAPACITY rule above.
  * cnt may be NULL in list mode.  In count mode with SIEVE_OUT_DEVICE, cnt is a
- * device pointer to one sieve_count_result. */
+ * device pointer to one sieve_count_result.  A range far up -- one whose base
+ * primes above the segment length would cost more to locate in every segment
+ * than to locate once and strike in a bitmap in global memory -- is run
+ * through the batch machinery as a one-query batch (see sieve_range_batch);
+ * the result is the same (except that SIEVE_ASYNC ranges always take the
+ * segment path). */
 int sieve_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, int mode, sieve_count_result *cnt,
                 uint64_t *out, size_t cap, size_t *n_out, unsigned flags);
 
@@ -185,8 +190,10 @@ int sieve_next(sieve_ctx *ctx, uint64_t after, size_t k, uint64_t *out, size_t *
  * many base primes above the tile length, "strips" that locate those primes
  * once per query (Table 1) and clear their hits in a global bitmap with
  * atomic ANDs -- and run by ONE persistent kernel launch that takes the items
- * in decreasing estimated cost from an atomic counter.  The launch and its
- * set-up / scan / compaction kernels are replayed as one CUDA graph.
+ * from an atomic counter: first the items of those "merged" queries, one
+ * query after another (so that its bitmap stays in L2), then the rest in
+ * decreasing estimated cost.  The launch and its set-up / finish / scan /
+ * compaction kernels are replayed as one CUDA graph.
  *
  * Inputs lo, hi, mode: HOST arrays of nq entries (the plan is built on the
  * host).  Outputs, host or device memory per SIEVE_OUT_DEVICE:
@@ -204,9 +211,10 @@ int sieve_range_batch(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, co
                       sieve_count_result *cnt, uint64_t *offsets, uint64_t *values, size_t cap,
                       size_t *n_values, unsigned flags);
 
-/* The same contract answered the plain way: one sieve_range call (its own
- * kernel launches and synchronisation) per query, in order.  It is the
- * comparison point for sieve_range_batch.  On CAPACITY, *n_values is exact
+/* The same contract answered the plain way: one segment-path range sieve
+ * (its own kernel launches and synchronisation, as sieve_range without the
+ * batch route) per query, in order.  It is the comparison point for
+ * sieve_range_batch.  On CAPACITY, *n_values is exact
  * (the queries past the capacity are counted but not listed). */
 int sieve_range_each(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, const uint8_t *mode, size_t nq,
                      sieve_count_result *cnt, uint64_t *offsets, uint64_t *values, size_t cap,

@@ -3,7 +3,7 @@
   python -m paper_2310_17746_gb300.cases count  LO HI [--seg W] [--reps R]
   python -m paper_2310_17746_gb300.cases list   LO HI [--reps R]
   python -m paper_2310_17746_gb300.cases primes32 N [--reps R]
-  python -m paper_2310_17746_gb300.cases batch  NQ [--seed S] [--count-only] [--reps R]
+  python -m paper_2310_17746_gb300.cases batch  NQ [--seed S] [--count-only] [--mix batch|serving] [--reps R]
 
 Numbers accept Python expressions such as 10**10+1 or 2**30.  Options may
 set tile_bits / block_threads / group_hits.  Prints one line per repetition
@@ -38,6 +38,9 @@ def main(argv=None) -> int:
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--count-only", action="store_true")
     ap.add_argument("--naive", action="store_true", help="batch: one range launch per query")
+    ap.add_argument("--mix", choices=["batch", "serving"], default="batch",
+                    help="batch: the 4096-query batch workload's distribution; serving: the serving "
+                         "workload's (lo up to 1e18, width up to 1e9, seed 1)")
     args = ap.parse_args(argv)
     if args.kind == "batch":
         return _batch(args)
@@ -84,13 +87,18 @@ def main(argv=None) -> int:
 
 def _batch(args) -> int:
     """The batched-range workload (log-uniform lo in [1e6, 1e15], width in
-    [1e3, 1e8], half list mode) with device outputs."""
+    [1e3, 1e8], half list mode), or the serving mix's queries (lo in [1e6,
+    1e18], width in [1e3, 1e9], list with probability 0.2), with device
+    outputs."""
     import numpy as np
     import torch
 
     from . import binding, workloads
 
-    q = workloads.batch_queries(n=args.a, seed=args.seed)
+    if args.mix == "serving":
+        q = workloads.serving_arrivals(1000.0, args.a, seed=args.seed or 1).queries
+    else:
+        q = workloads.batch_queries(n=args.a, seed=args.seed)
     if args.count_only:
         q.mode[:] = workloads.MODE_COUNT
     nq = len(q)

@@ -1,6 +1,7 @@
 // api.cu -- context lifetime, the device-resident base table, the wheel
 // pattern, and the public range calls of sieve.h.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -572,6 +573,30 @@ extern "C" int sieve_primes_u32(sieve_ctx *ctx, uint64_t n, uint32_t *out, size_
   return primes_common(ctx, n, out, cap, n_out, flags, 4);
 }
 
+// Whether [lo, hi) is better sieved with strips (batch path) than tile by
+// tile: the rule of the batch planner -- locating the primes above the tile
+// length once per tile costs more than locating them once and clearing their
+// hits with global atomics (priced 4x higher when the range's bitmap would
+// not fit half of L2).
+static bool strips_pay_off(const sieve_ctx *ctx, uint64_t lo, uint64_t hi) {
+  if (hi <= lo || hi > (1ull << 63)) return false;
+  const uint64_t s = isqrt_u64(hi - 1);
+  if (s > ctx->table.limit) return false;  // run_range reports RANGE
+  const uint64_t L = ctx->opt.batch_tile_bits ? ctx->opt.batch_tile_bits : ctx->opt.tile_bits;
+  const uint64_t span = (hi + 4) / 6 - lo / 6;
+  const uint64_t ntiles = (span + L - 1) / L;
+  if (ntiles < 2 || span >= (1ull << 31)) return false;
+  const uint32_t np = host_prime_count_le_table(ctx->table, s);
+  const uint32_t imid = host_prime_count_le_table(ctx->table, L);
+  if (np <= imid + 1) return false;
+  const uint32_t *P = ctx->table.host_primes;
+  const double large = (double)(np - imid);
+  const double hits = 2.0 * (double)span *
+                      (std::log(std::log((double)P[np - 1])) - std::log(std::log((double)P[imid])));
+  const double gcost = (double)span / 4.0 > 48e6 ? 160.0 : 40.0;
+  return 10.0 * large + gcost * hits < 10.0 * large * (double)ntiles;
+}
+
 extern "C" int sieve_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, int mode, sieve_count_result *cnt,
                            uint64_t *out, size_t cap, size_t *n_out, unsigned flags) {
   int rc = enter(ctx);
@@ -598,6 +623,22 @@ extern "C" int sieve_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, int mode, s
   rq.out_on_device = (flags & SIEVE_OUT_DEVICE) != 0;
   rq.total = cnt;
   rq.async = mode == SIEVE_COUNT && (flags & SIEVE_OUT_DEVICE) && (flags & SIEVE_ASYNC);
+  if (!rq.async && strips_pay_off(ctx, lo, hi)) {
+    // a range far up: run it as a one-query batch, whose planner locates the
+    // primes above the tile length once for the whole range (strips) instead
+    // of once per tile
+    const uint8_t m8 = (uint8_t)mode;
+    sieve_count_result local{0, 0};
+    uint64_t h_off[2] = {0, 0};
+    const bool dev = rq.out_on_device;
+    sieve_count_result *c = cnt ? cnt : (dev ? (sieve_count_result *)(ctx->d_acc + 4) : &local);
+    uint64_t *offs = dev ? (uint64_t *)(ctx->d_acc + 2) : h_off;
+    size_t n = 0;
+    rc = sieve_range_batch(ctx, &lo, &hi, &m8, 1, c, offs, mode == SIEVE_LIST ? out : nullptr,
+                           mode == SIEVE_LIST ? cap : 0, &n, flags & SIEVE_OUT_DEVICE);
+    if (n_out) *n_out = mode == SIEVE_LIST ? n : 0;
+    return rc;
+  }
   return run_range(ctx, ctx->table, rq, n_out);
 }
 

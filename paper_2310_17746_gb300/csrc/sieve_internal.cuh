@@ -30,7 +30,6 @@ constexpr uint32_t kFullMask = 0xFFFFFFFFu;
 // presieved prime.
 constexpr int kMaxPresieveGroups = 8;
 constexpr int kNumPatterns = 1 + kMaxPresieveGroups;
-constexpr uint32_t kPatternPadWords = 40;  // >= 33 words past each period end
 constexpr uint32_t kWheelPeriod = 5u * 7u * 11u * 13u * 17u * 19u;  // 1616615
 // the primes of each pattern (0-padded)
 constexpr uint32_t kPatternPrimes[kNumPatterns][6] = {
@@ -40,14 +39,9 @@ constexpr uint32_t kPatternPrimes[kNumPatterns][6] = {
 constexpr uint32_t pattern_period(int g) {
   return g == 0 ? kWheelPeriod : kPatternPrimes[g][0] * kPatternPrimes[g][1] * kPatternPrimes[g][2];
 }
-constexpr uint32_t pattern_words(int g) { return (pattern_period(g) + 31) / 32 + kPatternPadWords; }
 // index (in the table 2, 3, 5, ...) of the first prime struck after presieving
 // with the wheel and `groups` groups: 8 primes up to 19, then 3 per group
 __host__ __device__ constexpr uint32_t first_struck_prime_index(int groups) { return 8u + 3u * (uint32_t)groups; }
-// largest presieved prime
-__host__ __device__ constexpr uint32_t last_presieved_prime(int groups) {
-  return groups == 0 ? 19u : kPatternPrimes[groups][2];
-}
 
 // Per-pattern layout in the pattern buffer: class 1 at off1, class 5 at off5.
 struct PatternDesc {

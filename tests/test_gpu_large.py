@@ -68,3 +68,22 @@ def test_window_1e18_oracle():
         want = oracle.list_range(lo, hi, base=base)
         got = sv.range_list(lo, hi)
         assert np.array_equal(got, want)
+
+
+def test_far_range_takes_strips_and_matches():
+    """A range far up ([1e18, 1e18 + 2e7): 7 tiles, 5e7 base primes) is run as
+    a one-query batch with strips; it must equal both the tile-by-tile path
+    (one range launch through sieve_range_each) and the oracle."""
+    _need_gpu()
+    lo, hi = 10**18, 10**18 + 2 * 10**7
+    with binding.Sieve(hi) as sv:
+        got = sv.range_count(lo, hi)
+        lst = sv.range_list(lo, hi)
+        cnt_e, off_e, vals_e = sv.range_batch([lo], [hi], [1], naive=True)
+    assert (got.count, got.checksum) == (int(cnt_e[0][0]), int(cnt_e[0][1]))
+    np.testing.assert_array_equal(lst, vals_e)
+    want = oracle.count_range(lo, hi)
+    assert (got.count, got.checksum) == want
+    assert lst.size == want[0]
+    for x in lst[:: max(1, lst.size // 64)].tolist():
+        assert C.mr_is_prime(int(x))
