@@ -295,11 +295,19 @@ __global__ void __launch_bounds__(BLOCK) batch_scan_kernel(const BatchArena a) {
 
 // Write every list tile's primes in value order: to offsets[q] + (tile offset
 // within the query) in CSR mode, or to the query's out_base in fixed mode.
+// Whether the list compaction stages a tile's bitmap in shared memory (Wmax
+// pairs before the emission staging) or reads it from global memory.
+constexpr bool kBatchCompactSbuf = false;
+// batch tiles are small (few chunks per warp): the shallow staging row keeps
+// three CTAs per SM, measured faster than deeper rows
+constexpr uint32_t kBatchStageRow = 64;
+
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) batch_compact_kernel(const BatchArena a) {
   constexpr int NWARPS = BLOCK / 32;
   __shared__ uint32_t warp_cnt[NWARPS * 32];
-  extern __shared__ __align__(16) uint2 sbuf[];  // one tile's bitmap (up to Wmax pairs)
+  extern __shared__ __align__(16) uint2 sbuf[];  // [one tile's bitmap (up to Wmax pairs)] [emission staging]
+  uint16_t *stage = (uint16_t *)(sbuf + (kBatchCompactSbuf ? a.Wmax : 0));
   const char *plan = (const char *)a.plan;
   const BatchHeader *hdr = (const BatchHeader *)plan;
   const uint32_t n = hdr->nltiles;
@@ -328,8 +336,8 @@ __global__ void __launch_bounds__(BLOCK) batch_compact_kernel(const BatchArena a
       }
       off += e2 + e3;
     }
-    compact_tile<BLOCK, uint64_t>(a.list_bm + qd.bitmap_off + (uint64_t)qt.y * W, logW, K0, off, out, warp_cnt,
-                                  sbuf);
+    compact_tile<BLOCK, uint64_t, kBatchCompactSbuf, kBatchStageRow>(a.list_bm + qd.bitmap_off + (uint64_t)qt.y * W, logW, K0, off,
+                                                     out, warp_cnt, sbuf, stage);
     __syncthreads();
   }
 }
@@ -404,6 +412,11 @@ void *sieve_kernel_fn(int threads) {
 
 constexpr int kFinishThreads = 256;
 constexpr int kCompactThreads = 512;
+
+static size_t batch_compact_smem(uint32_t Wmax) {
+  return (kBatchCompactSbuf ? (size_t)Wmax * sizeof(uint2) : 0) +
+         compact_stage_bytes(kCompactThreads, kBatchStageRow);
+}
 constexpr int kScanThreads = 1024;
 
 // Launch shape for the context's current options: threads, largest tile,
@@ -498,9 +511,9 @@ int build_graph(BatchRunner &r) {
   kp.sharedMemBytes = 0;
   SIEVE_CUDA_TRY(cudaGraphAddKernelNode(&n_scan, g, &n_finish, 1, &kp));
   kp.func = (void *)batch_compact_kernel<kCompactThreads>;
-  kp.gridDim = dim3(r.ctx->num_sms * 2);
+  kp.gridDim = dim3(r.ctx->num_sms * 3);
   kp.blockDim = dim3(kCompactThreads);
-  kp.sharedMemBytes = (unsigned)((size_t)r.Wmax * sizeof(uint2));
+  kp.sharedMemBytes = (unsigned)batch_compact_smem(r.Wmax);
   SIEVE_CUDA_TRY(cudaGraphAddKernelNode(&n_compact, g, &n_scan, 1, &kp));
   SIEVE_CUDA_TRY(cudaGraphInstantiate(&r.exec, g, 0));
   r.n_copy = n_copy;
@@ -913,7 +926,7 @@ int batch_recompact(BatchRunner &r, uint64_t *values, uint64_t cap) {
                                  cudaMemcpyHostToDevice, r.stream));
   BatchArena a = arena_of(r);
   batch_compact_kernel<kCompactThreads>
-      <<<r.ctx->num_sms * 2, kCompactThreads, (size_t)r.Wmax * sizeof(uint2), r.stream>>>(a);
+      <<<r.ctx->num_sms * 3, kCompactThreads, batch_compact_smem(r.Wmax), r.stream>>>(a);
   r.ctx->launches++;
   SIEVE_CUDA_TRY(cudaGetLastError());
   return SIEVE_OK;

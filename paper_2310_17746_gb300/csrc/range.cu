@@ -199,14 +199,21 @@ struct CompactParams {
 
 // List compaction of a range in value order: one tile per CTA iteration
 // (compact_tile), after 2 and 3.
+// Whether the list compaction stages a tile's bitmap in shared memory (it
+// then needs W * 8 bytes of dynamic shared memory before the emission
+// staging) or reads it from global memory in both passes.
+constexpr bool kRangeCompactSbuf = false;
+constexpr uint32_t kRangeStageRow = 96;  // measured best of 64 / 96 / 128
+
 template <int BLOCK, typename OutT>
 __global__ void __launch_bounds__(BLOCK) compact_kernel(const CompactParams p) {
   constexpr int NWARPS = BLOCK / 32;
   __shared__ uint32_t warp_cnt[NWARPS * 32];
-  extern __shared__ __align__(16) uint2 sbuf[];  // one tile's bitmap (W pairs)
+  extern __shared__ __align__(16) uint2 sbuf[];  // [one tile's bitmap (W pairs)] [emission staging]
   if (p.offsets[p.ntiles] > p.cap) return;  // capacity: the host reports it
   OutT *out = (OutT *)p.out;
   const uint32_t W = p.L / 32;
+  uint16_t *stage = (uint16_t *)(sbuf + (kRangeCompactSbuf ? W : 0));
   for (uint32_t t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
     const uint64_t K0 = p.k_begin + (uint64_t)t * p.L;
     const uint2 *bm = p.bitmap + (uint64_t)t * W;
@@ -219,7 +226,7 @@ __global__ void __launch_bounds__(BLOCK) compact_kernel(const CompactParams p) {
       }
       off += (p.lo <= 2 && 2 < p.hi) + (p.lo <= 3 && 3 < p.hi);
     }
-    compact_tile<BLOCK, OutT>(bm, p.logW, K0, off, out, warp_cnt, sbuf);
+    compact_tile<BLOCK, OutT, kRangeCompactSbuf, kRangeStageRow>(bm, p.logW, K0, off, out, warp_cnt, sbuf, stage);
     __syncthreads();
   }
 }
@@ -227,6 +234,11 @@ __global__ void __launch_bounds__(BLOCK) compact_kernel(const CompactParams p) {
 // ---------------------------------------------------------------- host side
 
 constexpr int kCompactBlock = 512;
+
+// Dynamic shared memory of compact_kernel for tiles of L indices per class.
+static size_t compact_smem_bytes(uint32_t L) {
+  return (kRangeCompactSbuf ? (size_t)(L / 32) * sizeof(uint2) : 0) + compact_stage_bytes(kCompactBlock, kRangeStageRow);
+}
 
 namespace {
 
@@ -530,7 +542,7 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
   cp.offsets = offsets;
   cp.out = dst;
   cp.cap = req.cap;
-  const size_t csmem = (size_t)(L / 32) * sizeof(uint2);
+  const size_t csmem = compact_smem_bytes(L);
   const int cgrid = (int)std::min<uint64_t>(ntiles, (uint64_t)ctx->num_sms * 4);
   if (req.out_bytes == 4)
     compact_kernel<kCompactBlock, uint32_t><<<cgrid, kCompactBlock, csmem, st>>>(cp);
@@ -683,7 +695,7 @@ int run_range_list_into(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *out,
   cp.out = out;
   cp.cap = cap;
   const int cgrid = (int)std::min<uint64_t>(ntiles, (uint64_t)ctx->num_sms * 4);
-  compact_kernel<kCompactBlock, uint64_t><<<cgrid, kCompactBlock, (size_t)(L / 32) * sizeof(uint2), st>>>(cp);
+  compact_kernel<kCompactBlock, uint64_t><<<cgrid, kCompactBlock, compact_smem_bytes(L), st>>>(cp);
   ctx->launches++;
   SIEVE_CUDA_TRY(cudaGetLastError());
   SIEVE_CUDA_TRY(cudaStreamSynchronize(st));

@@ -298,36 +298,60 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, uint32_t lane) 
   return x;
 }
 
+// Staging for compact_tile's emission: per warp and row, up to ROW (>= 64:
+// one chunk's row holds at most 64 candidates) 16-bit codes ((chunk - c0) << 6
+// | j << 1 | class, in value order); rows are ROW + 2 codes apart so that the
+// 32 lanes' rows start in different banks.  A deeper staging row flushes less
+// often but holds fewer CTAs per SM.
+__host__ __device__ constexpr size_t compact_stage_bytes(int block, uint32_t row) {
+  return (size_t)(block / 32) * 32 * (row + 2) * sizeof(uint16_t);
+}
+
+// Bit i of x to bit 2 i.
+__device__ __forceinline__ uint64_t spread_bits(uint32_t x) {
+  uint64_t v = x;
+  v = (v | (v << 16)) & 0x0000FFFF0000FFFFull;
+  v = (v | (v << 8)) & 0x00FF00FF00FF00FFull;
+  v = (v | (v << 4)) & 0x0F0F0F0F0F0F0F0Full;
+  v = (v | (v << 2)) & 0x3333333333333333ull;
+  v = (v | (v << 1)) & 0x5555555555555555ull;
+  return v;
+}
+
 // Write the survivors of one tile, in value order, to out[off, ...).  The
 // tile's bitmap bm holds W = 2^logW (class-1 word, class-5 word) pairs in the
 // sliced layout: index k = b W + w is bit b of word w, so row b (bit b of
 // every word) is the index run [b W, b W + W), and value order is row-major.
-// The bitmap is staged in shared memory (sbuf, W pairs; bm 16-byte aligned).
+// With SBUF the bitmap is first staged in shared memory (sbuf, W pairs; bm
+// 16-byte aligned), else it is read from global memory in both passes.
 // Warp g takes the word chunks [g C / NWARPS, (g+1) C / NWARPS) of every row
 // (C = W / 32).  For a chunk, each lane loads one word pair and the warp
 // transposes the two 32 x 32 bit blocks, after which lane b holds row b's 32
 // candidates of each class for that chunk.  Pass 1: each lane counts its
 // row's survivors over the warp's chunks (warp_cnt[g][b], NWARPS x 32
 // entries), and the offsets follow from a row-major prefix sum.  Pass 2
-// writes the values (below).  Bits outside the valid range must already be
+// (below) writes the values.  Bits outside the valid range must already be
 // clear.
-template <int BLOCK, typename OutT>
+template <int BLOCK, typename OutT, bool SBUF, uint32_t ROW>
 __device__ __forceinline__ void compact_tile(const uint2 *__restrict__ bm, uint32_t logW, uint64_t K0, uint64_t off,
-                                             OutT *out, uint32_t *warp_cnt, uint2 *sbuf) {
+                                             OutT *out, uint32_t *warp_cnt, uint2 *sbuf, uint16_t *stage) {
   constexpr int NWARPS = BLOCK / 32;
+  constexpr uint32_t kPitch = ROW + 2;
+  static_assert(ROW >= 64, "a staging row must hold one chunk's row");
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t W = 1u << logW, C = W / 32;
-  {
+  if (SBUF) {
     const uint4 *src = (const uint4 *)bm;
     uint4 *dst = (uint4 *)sbuf;
     for (uint32_t i = threadIdx.x; i < W / 2; i += BLOCK) dst[i] = __ldg(src + i);
+    __syncthreads();
   }
-  __syncthreads();
+  auto pair = [&](uint32_t c) -> uint2 { return SBUF ? sbuf[(c << 5) + lane] : __ldg(bm + (c << 5) + lane); };
   const uint32_t c_begin = (uint32_t)((uint64_t)warp * C / NWARPS);
   const uint32_t c_end = (uint32_t)((uint64_t)(warp + 1) * C / NWARPS);
   uint32_t cnt = 0;
   for (uint32_t c = c_begin; c < c_end; c++) {
-    const uint2 x = sbuf[(c << 5) + lane];
+    const uint2 x = pair(c);
     cnt += __popc(warp_transpose32(x.x, lane)) + __popc(warp_transpose32(x.y, lane));
   }
   warp_cnt[warp * 32 + lane] = cnt;
@@ -349,31 +373,47 @@ __device__ __forceinline__ void compact_tile(const uint2 *__restrict__ bm, uint3
     }
   }
   __syncthreads();
-  // Pass 2, chunk by chunk: lane b keeps row b's running output position;
-  // for each row the warp receives the row's two masks and position by
-  // shuffles, and lane j writes the values of its own index -- consecutive
-  // lanes, consecutive outputs, so the stores coalesce.
+  // Pass 2.  The warp's outputs of row b form one run, starting at pos (lane
+  // b's register).  Lane b extracts its row's survivors of each chunk, in
+  // value order, as codes into its staging row; before a chunk would overflow
+  // a row, the warp flushes: row by row, consecutive lanes write consecutive
+  // outputs, so the stores coalesce and use all lanes.
   uint32_t pos = warp_cnt[warp * 32 + lane];
-  const uint32_t lt = (1u << lane) - 1u;  // lanes below this one
+  uint16_t *const wst = stage + (size_t)warp * 32 * kPitch;
+  uint16_t *const row = wst + lane * kPitch;
   const uint64_t v0 = 6 * K0;
-  for (uint32_t c = c_begin; c < c_end; c++) {
-    const uint2 x = sbuf[(c << 5) + lane];
-    const uint32_t t1 = warp_transpose32(x.x, lane), t5 = warp_transpose32(x.y, lane);
-    const uint32_t row_n = __popc(t1) + __popc(t5);
-#pragma unroll 4
-    for (uint32_t b = 0; b < 32; b++) {
-      const uint32_t m1 = __shfl_sync(kFullMask, t1, b), m5 = __shfl_sync(kFullMask, t5, b);
-      const uint32_t base = __shfl_sync(kFullMask, pos, b);
-      const uint32_t s1 = (m1 >> lane) & 1u, s5 = (m5 >> lane) & 1u;
-      if (s1 | s5) {
-        OutT *o = out + off + base + __popc(m1 & lt) + __popc(m5 & lt);
-        const uint64_t v = v0 + 6ull * ((b << logW) + (c << 5) + lane);
-        if (s1) *o++ = (OutT)(v + 1);
-        if (s5) *o = (OutT)(v + 5);
+  uint32_t n = 0, c0 = c_begin;
+  auto flush = [&]() {
+    __syncwarp();
+    for (uint32_t r = 0; r < 32; r++) {
+      const uint32_t nr = __shfl_sync(kFullMask, n, r), pr = __shfl_sync(kFullMask, pos, r);
+      const uint16_t *rs = wst + r * kPitch;
+      const uint64_t vr = v0 + 6ull * (((uint64_t)r << logW) + ((uint64_t)c0 << 5));
+      for (uint32_t i = lane; i < nr; i += 32) {
+        const uint32_t code = rs[i];
+        out[off + pr + i] = (OutT)(vr + 6ull * (code >> 1) + 1 + 4 * (code & 1));
       }
     }
-    pos += row_n;
+    __syncwarp();
+    pos += n;
+    n = 0;
+  };
+  for (uint32_t c = c_begin; c < c_end; c++) {
+    const uint2 x = pair(c);
+    const uint32_t t1 = warp_transpose32(x.x, lane), t5 = warp_transpose32(x.y, lane);
+    const uint32_t rn = __popc(t1) + __popc(t5);
+    if (__any_sync(kFullMask, n + rn > ROW) || c - c0 >= 1024) {  // codes hold c - c0 < 1024
+      flush();
+      c0 = c;
+    }
+    uint64_t m = spread_bits(t1) | (spread_bits(t5) << 1);
+    const uint32_t cb = (c - c0) << 6;
+    while (m) {
+      row[n++] = (uint16_t)(cb + (uint32_t)(__ffsll((long long)m) - 1));
+      m &= m - 1;
+    }
   }
+  flush();
 }
 
 }  // namespace sieve
