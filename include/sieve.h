@@ -354,6 +354,17 @@ int sieve_measure_smem_atomics(int device, double *conflict_free, double *random
  * INVALID if B % 6 != 0, M < B, P < 5 or P % 6 not in {1, 5}. */
 int sieve_table1_start(uint64_t B, uint64_t M, uint32_t P, int64_t *id1, int64_t *id5);
 
+/* Host evaluation of the other start-index routine the kernels run: the
+ * per-tile starts of Section 3 for a tile whose index 0 stands for value B
+ * (M = B), from a per-prime inverse of 6 instead of Table 1's case split.
+ * Index k of class r stands for 6 (B / 6 + k) + r, which P divides iff
+ * B / 6 + k = -r / 6 (mod P), so the first such k is
+ * (c_r - (B / 6) mod P) mod P with c_r = (-r / 6) mod P.  The one-lane
+ * strike band uses it whenever P^2 <= B (then it equals Table 1's start).
+ * Requires B % 6 == 0, 5 <= P < 2^31, P % 6 in {1, 5} and P^2 <= B, else
+ * INVALID. */
+int sieve_inverse6_start(uint64_t B, uint32_t P, uint32_t *id1, uint32_t *id5);
+
 #ifdef __cplusplus
 }
 #endif

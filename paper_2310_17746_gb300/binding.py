@@ -99,6 +99,8 @@ SIGNATURES = {
     "sieve_segment_counts": (_i, [_p, _u64, _u64, _u64, _p, _sz, _p, _u]),
     "sieve_table1_start": (_i, [_u64, _u64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int64),
                                 ctypes.POINTER(ctypes.c_int64)]),
+    "sieve_inverse6_start": (_i, [_u64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32),
+                                  ctypes.POINTER(ctypes.c_uint32)]),
     "sieve_range_list_noalloc": (_i, [_p, _u64, _u64, _p, _sz, ctypes.POINTER(_sz), _p]),
     "sieve_range_batch": (_i, [_p, _p, _p, _p, _sz, _p, _p, _p, _sz, ctypes.POINTER(_sz), _u]),
     "sieve_range_each": (_i, [_p, _p, _p, _p, _sz, _p, _p, _p, _sz, ctypes.POINTER(_sz), _u]),
@@ -143,6 +145,14 @@ def table1_start(B: int, M: int, P: int) -> tuple[int, int]:
     a = ctypes.c_int64(0)
     b = ctypes.c_int64(0)
     _check(lib().sieve_table1_start(B, M, P, ctypes.byref(a), ctypes.byref(b)), "sieve_table1_start")
+    return a.value, b.value
+
+
+def inverse6_start(B: int, P: int) -> tuple[int, int]:
+    """Host evaluation of the kernels' inverse-of-6 start-index routine."""
+    a = ctypes.c_uint32(0)
+    b = ctypes.c_uint32(0)
+    _check(lib().sieve_inverse6_start(B, P, ctypes.byref(a), ctypes.byref(b)), "sieve_inverse6_start")
     return a.value, b.value
 
 

@@ -105,9 +105,15 @@ __global__ void sliced_pattern_kernel(uint32_t *pat, const SlicedGenArgs a) {
   pat[a.off5 + j] = w5;
 }
 
-__global__ void reciprocal_kernel(const uint32_t *__restrict__ primes, uint64_t *__restrict__ magic, uint32_t n) {
+// Per-prime constants of the base table: the invariant-division reciprocal
+// and the inverse-of-6 start constants.
+__global__ void reciprocal_kernel(const uint32_t *__restrict__ primes, uint64_t *__restrict__ magic,
+                                  uint2 *__restrict__ cinv, uint32_t n) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) magic[i] = reciprocal64(primes[i]);
+  if (i < n) {
+    magic[i] = reciprocal64(primes[i]);
+    cinv[i] = inverse6_constants(primes[i]);
+  }
 }
 
 // Host Eratosthenes for the first, small part of the base table.
@@ -206,6 +212,7 @@ static void free_ctx(sieve_ctx *c) {
   cudaFree(c->d_psets);
   cudaFree(c->d_primes);
   cudaFree(c->d_magic);
+  cudaFree(c->d_cinv);
   for (auto &ss : c->sliced) cudaFree(ss.d);
   cudaFree(c->d_acc);
   cudaFree(c->d_scratch);
@@ -274,16 +281,18 @@ static int build_base_table(sieve_ctx *c, uint64_t limit) {
   const uint64_t cap = pi_upper(limit);
   SIEVE_CUDA_TRY(cudaMalloc(&c->d_primes, cap * sizeof(uint32_t)));
   SIEVE_CUDA_TRY(cudaMalloc(&c->d_magic, cap * sizeof(uint64_t)));
+  SIEVE_CUDA_TRY(cudaMalloc(&c->d_cinv, cap * sizeof(uint2)));
   SIEVE_CUDA_TRY(cudaMemcpyAsync(c->d_primes, small.data(), small.size() * sizeof(uint32_t),
                                  cudaMemcpyHostToDevice, c->stream));
   const uint32_t ns = (uint32_t)small.size();
-  reciprocal_kernel<<<(ns + 255) / 256, 256, 0, c->stream>>>(c->d_primes, c->d_magic, ns);
+  reciprocal_kernel<<<(ns + 255) / 256, 256, 0, c->stream>>>(c->d_primes, c->d_magic, c->d_cinv, ns);
   c->launches++;
   SIEVE_CUDA_TRY(cudaGetLastError());
 
   DeviceTable t0;
   t0.primes = c->d_primes;
   t0.magic = c->d_magic;
+  t0.cinv = c->d_cinv;
   t0.host_primes = small.data();
   t0.nprimes = ns;
   t0.limit = small_n;
@@ -303,7 +312,7 @@ static int build_base_table(sieve_ctx *c, uint64_t limit) {
     total += n;
     if (n) {
       reciprocal_kernel<<<(uint32_t)((n + 255) / 256), 256, 0, c->stream>>>(c->d_primes + ns, c->d_magic + ns,
-                                                                           (uint32_t)n);
+                                                                           c->d_cinv + ns, (uint32_t)n);
       c->launches++;
       SIEVE_CUDA_TRY(cudaGetLastError());
     }
@@ -314,6 +323,7 @@ static int build_base_table(sieve_ctx *c, uint64_t limit) {
   SIEVE_CUDA_TRY(cudaStreamSynchronize(c->stream));
   c->table.primes = c->d_primes;
   c->table.magic = c->d_magic;
+  c->table.cinv = c->d_cinv;
   c->table.host_primes = c->h_primes.data();
   c->table.nprimes = (uint32_t)total;
   c->table.limit = limit;
@@ -335,11 +345,14 @@ int extend_base_table(sieve_ctx *c, uint64_t new_limit) {
   const uint64_t cap = pi_upper(new_limit);
   uint32_t *np_ = nullptr;
   uint64_t *nm = nullptr;
+  uint2 *nc = nullptr;
   SIEVE_CUDA_TRY(cudaStreamSynchronize(c->stream));
   SIEVE_CUDA_TRY(cudaMalloc(&np_, cap * sizeof(uint32_t)));
   cudaError_t e = cudaMalloc(&nm, cap * sizeof(uint64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&nc, cap * sizeof(uint2));
   if (e != cudaSuccess) {
     cudaFree(np_);
+    cudaFree(nm);
     return cuda_fail(e, "cudaMalloc (base table)");
   }
   const uint32_t n0 = c->table.nprimes;
@@ -349,6 +362,8 @@ int extend_base_table(sieve_ctx *c, uint64_t new_limit) {
     if ((e = cudaMemcpyAsync(np_, c->d_primes, n0 * sizeof(uint32_t), cudaMemcpyDeviceToDevice, c->stream)) !=
             cudaSuccess ||
         (e = cudaMemcpyAsync(nm, c->d_magic, n0 * sizeof(uint64_t), cudaMemcpyDeviceToDevice, c->stream)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(nc, c->d_cinv, n0 * sizeof(uint2), cudaMemcpyDeviceToDevice, c->stream)) !=
             cudaSuccess) {
       rc = cuda_fail(e, "cudaMemcpyAsync (base table)");
       break;
@@ -363,7 +378,8 @@ int extend_base_table(sieve_ctx *c, uint64_t new_limit) {
     rq.out_on_device = 1;
     if ((rc = run_range(c, c->table, rq, &n)) != SIEVE_OK) break;
     if (n) {
-      reciprocal_kernel<<<(uint32_t)((n + 255) / 256), 256, 0, c->stream>>>(np_ + n0, nm + n0, (uint32_t)n);
+      reciprocal_kernel<<<(uint32_t)((n + 255) / 256), 256, 0, c->stream>>>(np_ + n0, nm + n0, nc + n0,
+                                                                           (uint32_t)n);
       c->launches++;
       if ((e = cudaGetLastError()) != cudaSuccess) {
         rc = cuda_fail(e, "reciprocal_kernel");
@@ -382,14 +398,18 @@ int extend_base_table(sieve_ctx *c, uint64_t new_limit) {
     c->h_primes.resize(n0);
     cudaFree(np_);
     cudaFree(nm);
+    cudaFree(nc);
     return rc;
   }
   cudaFree(c->d_primes);
   cudaFree(c->d_magic);
+  cudaFree(c->d_cinv);
   c->d_primes = np_;
   c->d_magic = nm;
+  c->d_cinv = nc;
   c->table.primes = np_;
   c->table.magic = nm;
+  c->table.cinv = nc;
   c->table.host_primes = c->h_primes.data();
   c->table.nprimes = (uint32_t)(n0 + n);
   c->table.limit = new_limit;
@@ -664,6 +684,16 @@ extern "C" int sieve_segment_counts(sieve_ctx *ctx, uint64_t lo, uint64_t hi, ui
 }
 
 // ---------------------------------------------------------------- table 1 (host)
+
+extern "C" int sieve_inverse6_start(uint64_t B, uint32_t P, uint32_t *id1, uint32_t *id5) {
+  if (!id1 || !id5 || B % 6 != 0 || P < 5 || (P % 6 != 1 && P % 6 != 5) || P >= 0x80000000u ||
+      (uint64_t)P * P > B || B >= (1ull << 63)) {
+    set_error("sieve_inverse6_start: invalid argument");
+    return SIEVE_ERR_INVALID;
+  }
+  starts_from_inverse(B / 6, P, reciprocal64(P), inverse6_constants(P), *id1, *id5);
+  return SIEVE_OK;
+}
 
 extern "C" int sieve_table1_start(uint64_t B, uint64_t M, uint32_t P, int64_t *id1, int64_t *id5) {
   if (!id1 || !id5 || B % 6 != 0 || M < B || P < 5 || (P % 6 != 1 && P % 6 != 5) ||

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK > 0 ? 1024 / BLOCK : 1)) 
     const uint32_t split = qd.i_split < it.i1 ? qd.i_split : it.i1;
     warp_band_starts<BLOCK>(starts, B, tg.len, a.primes, a.magic, it.i0, split);
     __syncthreads();
-    strike_primes<BLOCK>(s1, s5, B, tg, a.primes, a.magic, starts, it.i0, split, sh_np, &sh_next);
+    strike_primes<BLOCK>(s1, s5, B, tg, a.primes, a.magic, a.cinv, starts, it.i0, split, sh_np, &sh_next);
     __syncthreads();
     if (merged) {
       // AND the shared-memory result into the query's bitmap in global memory
@@ -396,6 +396,7 @@ BatchArena arena_of(const BatchRunner &r) {
   a.list_bm = r.d_list_bm;
   a.primes = r.ctx->table.primes;
   a.magic = r.ctx->table.magic;
+  a.cinv = r.ctx->table.cinv;
   a.psets = r.ctx->d_psets;
   a.Wmax = r.Wmax;
   a.band_max = r.band_max;

@@ -91,6 +91,7 @@ struct BatchArena {
   uint2 *list_bm;           // list tiles' bitmaps
   const uint32_t *primes;
   const uint64_t *magic;
+  const uint2 *cinv;
   const PatternSetDev *psets;  // indexed by log2(W)
   uint32_t Wmax;               // words per class of the largest tile
   uint32_t band_max;           // warp-band start slots in shared memory

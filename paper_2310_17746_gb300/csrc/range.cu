@@ -23,6 +23,7 @@ struct RangeKernelParams {
   uint32_t ntiles;
   const uint32_t *primes;
   const uint64_t *magic;
+  const uint2 *cinv;
   uint32_t nprimes;         // primes[0..nprimes) cover isqrt(hi - 1)
   uint32_t i_first;         // first prime index struck (after the presieved ones)
   uint32_t i_split;         // primes with index < i_split are struck by a warp
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
     warp_band_starts<BLOCK>(starts, B, tg.len, p.primes, p.magic, p.i_first, p.i_split);
     __syncthreads();
 
-    strike_primes<BLOCK>(s1, s5, B, tg, p.primes, p.magic, starts, p.i_first, p.i_split, sh_np, &sh_next);
+    strike_primes<BLOCK>(s1, s5, B, tg, p.primes, p.magic, p.cinv, starts, p.i_first, p.i_split, sh_np, &sh_next);
     __syncthreads();
 
     const ValidRange v = valid_range(p.lo, p.hi, B, tg.len);
@@ -422,6 +423,7 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
   p.ntiles = ntiles;
   p.primes = table.primes;
   p.magic = table.magic;
+  p.cinv = table.cinv;
   p.nprimes = np;
   p.i_split = i_split;
   p.i_first = i_first;
@@ -648,6 +650,7 @@ int run_range_list_into(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *out,
   p.ntiles = ntiles;
   p.primes = table.primes;
   p.magic = table.magic;
+  p.cinv = table.cinv;
   p.nprimes = np;
   p.i_first = i_first;
   p.i_split = i_split;

@@ -223,11 +223,38 @@ __host__ __device__ __forceinline__ bool tile_starts_within(uint64_t B, uint32_t
   return true;
 }
 
+// The same start indices from a per-prime inverse of 6.  Class r's index k
+// holds value 6 (K0 + k) + r, which P divides iff K0 + k = -r / 6 (mod P);
+// so with c_r = (-r / 6) mod P (a per-prime constant) the first such k >= 0
+// is (c_r - K0 mod P) mod P.  This equals the Table 1 start whenever P^2 <=
+// 6 K0 (no clamp; the start lies below P), and costs one invariant-division
+// remainder and a few 32-bit operations instead of the table's case split.
+// 6^{-1} mod P is (P + 1) / 6 for P = 5 (mod 6) and (5 P + 1) / 6 for P = 1.
+__host__ __device__ __forceinline__ uint2 inverse6_constants(uint32_t P) {
+  if (P < 5) return make_uint2(0, 0);
+  const uint64_t inv6 = P % 6u == 5u ? ((uint64_t)P + 1) / 6 : (5ull * P + 1) / 6;
+  const uint64_t c1 = P - inv6;                  // -1/6 mod P (inv6 in [1, P))
+  const uint64_t i5 = (5 * inv6) % P;            // 5/6 mod P
+  const uint64_t c5 = i5 == 0 ? 0 : P - i5;      // -5/6 mod P
+  return make_uint2((uint32_t)c1, (uint32_t)c5);
+}
+
+// k1 / k5 = (c - K0 mod P) mod P for P < 2^31 (m = reciprocal64(P)).
+__host__ __device__ __forceinline__ void starts_from_inverse(uint64_t K0, uint32_t P, uint64_t m, uint2 c,
+                                                             uint32_t &k1, uint32_t &k5) {
+  const uint64_t q = mulhi64(K0, m);  // floor(K0 / P) or one less
+  uint32_t r = (uint32_t)K0 - (uint32_t)q * P;  // exact: K0 - q P < 2 P < 2^32
+  if (r >= P) r -= P;
+  k1 = c.x >= r ? c.x - r : c.x - r + P;
+  k5 = c.y >= r ? c.y - r : c.y - r + P;
+}
+
 // ---------------------------------------------------------------- context
 
 struct DeviceTable {
   const uint32_t *primes = nullptr;       // device: 2, 3, 5, 7, ... (all primes <= limit)
   const uint64_t *magic = nullptr;        // device: reciprocal64(primes[i])
+  const uint2 *cinv = nullptr;            // device: inverse6_constants(primes[i])
   const uint32_t *host_primes = nullptr;  // host copy of primes
   uint32_t nprimes = 0;
   uint64_t limit = 0;
@@ -249,6 +276,7 @@ struct sieve_ctx {
   sieve::DeviceTable table;    // views into the buffers below
   uint32_t *d_primes = nullptr;
   uint64_t *d_magic = nullptr;
+  uint2 *d_cinv = nullptr;
   std::vector<uint32_t> h_primes;  // host copy of the base table
   // presieve patterns in the sliced layout, one set per tile width W = 2^logW
   struct SlicedSet {

@@ -131,12 +131,17 @@ __device__ __forceinline__ void warp_band_starts(uint2 *starts, uint64_t B, uint
 // warp (lane l takes hits l, l + 32, ... of the prime; bank-conflict free in
 // the sliced layout) from the starts precomputed in shared memory, handed out
 // one at a time through a shared counter so that warps finish together; the
-// rest by one lane each.
+// rest by one lane each, which locates the prime's first hits from its
+// inverse-of-6 constants (cinv; the Table 1 start, see starts_from_inverse)
+// or, where the P^2 clamp can apply, with Table 1 itself.  (Loading the
+// constants only for primes below the tile span, so that larger ones keep a
+// one-remainder miss test, was slower: the load then waits for the prime.)
 template <int BLOCK>
 __device__ __forceinline__ void strike_primes(uint32_t *s1, uint32_t *s5, uint64_t B, const TileGeom &tg,
                                               const uint32_t *__restrict__ primes,
-                                              const uint64_t *__restrict__ magic, const uint2 *starts,
-                                              uint32_t i_first, uint32_t i_split, uint32_t np, uint32_t *next) {
+                                              const uint64_t *__restrict__ magic, const uint2 *__restrict__ cinv,
+                                              const uint2 *starts, uint32_t i_first, uint32_t i_split, uint32_t np,
+                                              uint32_t *next) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t split = i_split < np ? i_split : np;
   const uint32_t len = tg.len, wmask = tg.W - 1, logW = tg.logW, span6 = 6 * tg.len;
@@ -153,33 +158,44 @@ __device__ __forceinline__ void strike_primes(uint32_t *s1, uint32_t *s5, uint64
   }
   // one lane per prime; the next prime's table entries are loaded before the
   // current prime is struck so that their latency overlaps the strikes
+  const uint64_t K0 = B / 6;
   uint32_t i = (split > i_first ? split : i_first) + threadIdx.x;
   uint32_t P = 0;
   uint64_t m = 0;
+  uint2 c = make_uint2(0, 0);
   if (i < np) {
     P = __ldg(primes + i);
     m = __ldg(magic + i);
+    c = __ldg(cinv + i);
   }
   while (i < np) {
     const uint32_t in = i + BLOCK;
     uint32_t Pn = 0;
     uint64_t mn = 0;
+    uint2 cn = make_uint2(0, 0);
     if (in < np) {
       Pn = __ldg(primes + in);
       mn = __ldg(magic + in);
+      cn = __ldg(cinv + in);
     }
-    uint64_t k1, k5;
-    if (tile_starts_within(B, P, m, span6, k1, k5)) {
-      // a plain loop per class: lane-band primes have few hits per tile, so
-      // the unrolled loop's set-up costs more than it saves (measured)
-      if (k1 < len)  // k1, k5 may exceed 2^32 on the general path; k + P < 2^32 (P < 2^31.6)
-        for (uint32_t k = (uint32_t)k1; k < len; k += P) strike_one(s1, k, wmask, logW);
-      if (k5 < len)
-        for (uint32_t k = (uint32_t)k5; k < len; k += P) strike_one(s5, k, wmask, logW);
+    uint32_t k1 = len, k5 = len;
+    if ((uint64_t)P * P <= B && P < 0x80000000u) {
+      starts_from_inverse(K0, P, m, c, k1, k5);  // < P < 2^31
+    } else {
+      uint64_t a1, a5;
+      if (tile_starts_within(B, P, m, span6, a1, a5)) {
+        k1 = a1 < len ? (uint32_t)a1 : len;
+        k5 = a5 < len ? (uint32_t)a5 : len;
+      }
     }
+    // a plain loop per class: lane-band primes have few hits per tile, so the
+    // unrolled loop's set-up costs more than it saves (measured); k + P < 2^32
+    for (uint32_t k = k1; k < len; k += P) strike_one(s1, k, wmask, logW);
+    for (uint32_t k = k5; k < len; k += P) strike_one(s5, k, wmask, logW);
     i = in;
     P = Pn;
     m = mn;
+    c = cn;
   }
 }
 

@@ -80,3 +80,41 @@ def test_invalid_arguments():
     for args in ((1, 1, 7), (0, 0, 4), (0, 0, 9), (12, 6, 7), (0, 0, 3)):
         with pytest.raises(binding.SieveError):
             binding.table1_start(*args)
+
+
+def _check_inverse(B, P):
+    id1, id5 = binding.inverse6_start(B, P)
+    assert B + 6 * id1 + 1 == oracle.first_class_multiple(B, P, 1, True), (B, P)
+    assert B + 6 * id5 + 5 == oracle.first_class_multiple(B, P, 5, True), (B, P)
+    assert (id1, id5) == binding.table1_start(B, B, P), (B, P)
+
+
+def test_inverse6_start_matches_definition_and_table1():
+    """The one-lane band's starts from (-r / 6) mod P equal the smallest
+    class-r multiple >= B (and Table 1's tile starts) whenever P^2 <= B, in
+    every residue of B / 6 mod P and P mod 6."""
+    rng = np.random.default_rng(17)
+    primes = [p for p in range(5, 3000) if C.td_is_prime(p)]
+    seen = set()
+    for P in primes:
+        for _ in range(8):
+            B = 6 * int(rng.integers((P * P + 5) // 6, 10**15))
+            _check_inverse(B, P)
+            seen.add((P % 6, (B // 6) % P == 0))
+        B = 6 * ((P * P + 5) // 6)  # the first tile base at or above P^2
+        _check_inverse(B, P)
+        _check_inverse(6 * P * P, P)  # B / 6 = 0 (mod P)
+    assert seen >= {(1, False), (5, False)}
+    for P in (65521, 999983, 1000003, 2147483647, 2147483629):
+        for scale in (10**13, 10**18, 2**62):
+            low = -(-P * P // 6)  # B >= P^2
+            if low >= scale // 6:
+                continue
+            for _ in range(20):
+                _check_inverse(6 * int(rng.integers(low, scale // 6)), P)
+
+
+def test_inverse6_start_rejects_outside_its_domain():
+    for B, P in ((6, 7), (48, 7), (100 * 6 + 1, 7), (6 * 10**6, 4), (6 * 10**6, 9), (2**62, 2**31 + 11)):
+        with pytest.raises(binding.SieveError):
+            binding.inverse6_start(B, P)
