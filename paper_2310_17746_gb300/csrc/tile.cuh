@@ -168,34 +168,45 @@ __device__ __forceinline__ void strike_primes(uint32_t *s1, uint32_t *s5, uint64
     m = __ldg(magic + i);
     c = __ldg(cinv + i);
   }
-  while (i < np) {
-    const uint32_t in = i + BLOCK;
-    uint32_t Pn = 0;
-    uint64_t mn = 0;
-    uint2 cn = make_uint2(0, 0);
-    if (in < np) {
-      Pn = __ldg(primes + in);
-      mn = __ldg(magic + in);
-      cn = __ldg(cinv + in);
-    }
+  // the loop is unrolled by two with the prefetched entries alternating
+  // between two register sets (fewer moves than rotating one set; measured)
+  auto one = [&](uint32_t Pq, uint64_t mq, uint2 cq) {
     uint32_t k1 = len, k5 = len;
-    if ((uint64_t)P * P <= B && P < 0x80000000u) {
-      starts_from_inverse(K0, P, m, c, k1, k5);  // < P < 2^31
+    if ((uint64_t)Pq * Pq <= B && Pq < 0x80000000u) {
+      starts_from_inverse(K0, Pq, mq, cq, k1, k5);
     } else {
       uint64_t a1, a5;
-      if (tile_starts_within(B, P, m, span6, a1, a5)) {
+      if (tile_starts_within(B, Pq, mq, span6, a1, a5)) {
         k1 = a1 < len ? (uint32_t)a1 : len;
         k5 = a5 < len ? (uint32_t)a5 : len;
       }
     }
-    // a plain loop per class: lane-band primes have few hits per tile, so the
-    // unrolled loop's set-up costs more than it saves (measured); k + P < 2^32
-    for (uint32_t k = k1; k < len; k += P) strike_one(s1, k, wmask, logW);
-    for (uint32_t k = k5; k < len; k += P) strike_one(s5, k, wmask, logW);
-    i = in;
-    P = Pn;
-    m = mn;
-    c = cn;
+    // a plain loop per class: lane-band primes have few hits per tile, so
+    // the unrolled loop's set-up costs more than it saves (measured); k + P
+    // < 2^32
+    for (uint32_t k = k1; k < len; k += Pq) strike_one(s1, k, wmask, logW);
+    for (uint32_t k = k5; k < len; k += Pq) strike_one(s5, k, wmask, logW);
+  };
+  while (i < np) {
+    const uint32_t in = i + BLOCK;
+    uint32_t Pb = 0;
+    uint64_t mb = 0;
+    uint2 cb = make_uint2(0, 0);
+    if (in < np) {
+      Pb = __ldg(primes + in);
+      mb = __ldg(magic + in);
+      cb = __ldg(cinv + in);
+    }
+    one(P, m, c);
+    if (in >= np) break;
+    const uint32_t in2 = in + BLOCK;
+    if (in2 < np) {
+      P = __ldg(primes + in2);
+      m = __ldg(magic + in2);
+      c = __ldg(cinv + in2);
+    }
+    one(Pb, mb, cb);
+    i = in2;
   }
 }
 
