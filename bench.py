@@ -46,6 +46,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-queries leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-list", action="store_true", help="skip the list leg")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
@@ -114,9 +115,9 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel_file: str):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel sources
-    are unchanged since it was taken (else None)."""
+def profiled_traffic(kernel_file: str, key: str = "dram_bytes_per_launch_full"):
+    """DRAM bytes (per launch, or the given key) from a committed ncu summary,
+    if the kernel sources are unchanged since it was taken (else None)."""
     path = os.path.join(ROOT, "profiles", kernel_file)
     try:
         with open(path) as f:
@@ -125,7 +126,7 @@ def profiled_traffic(kernel_file: str):
         return None
     if d.get("source_hash") != source_hash():
         return None
-    return d.get("dram_bytes_per_launch_full")
+    return d.get(key)
 
 
 # ---------------------------------------------------------------- clocks
@@ -332,6 +333,64 @@ def batch_leg(steps: int, warmup: int) -> dict:
     }
 
 
+def list_leg(steps: int, warmup: int) -> dict:
+    """The list path: the uint64 primes of [1e12, 1e12 + 2e10) written into a
+    device buffer through sieve_range, with the tile kernel and the compaction
+    timed by the library's phase events.  Roofline of the compaction: the HBM
+    bytes it must move (8 B per listed prime written, each tile's bitmap read
+    once) over its device time, against the measured copy bandwidth."""
+    import numpy as np
+    import torch
+
+    from paper_2310_17746_gb300 import binding
+
+    lo, hi = 10**12, 10**12 + 2 * 10**10
+    sv = binding.Sieve(hi)
+    n = sv.range_count(lo, hi).count
+    out = torch.empty(max(n, 1), dtype=torch.int64, device="cuda")
+    sv.set_phase_timing(True)
+    for _ in range(max(1, warmup)):
+        sv.range_list(lo, hi, out=out)
+    st = torch.cuda.current_stream()
+    calls, phases = [], []
+    for _ in range(steps):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        s.record(st)
+        got = sv.range_list(lo, hi, out=out)
+        e.record(st)
+        torch.cuda.synchronize()
+        calls.append(s.elapsed_time(e) / 1e3)
+        phases.append(sv.phase_times())
+        assert got == n, (got, n)
+    head = out[:4].cpu().numpy()
+    tail = out[n - 2:n].cpu().numpy()
+    assert head[0] == 1000000000039 and (np.diff(head) > 0).all() and tail[-1] < hi, (head, tail)
+    sv.close()
+    ph = phases[-1]
+    compact_s = statistics.mean(p["compact_ms"] for p in phases) / 1e3
+    sieve_s = statistics.mean(p["sieve_ms"] for p in phases) / 1e3
+    bitmap_bytes = int(ph["tiles"]) * (int(ph["tile_len"]) // 32) * 8
+    alg_bytes = n * 8 + bitmap_bytes
+    achieved = alg_bytes / compact_s / 1e9
+    peaks = measured_peaks()
+    peak = float(peaks.get("hbm_gbs") or 6800.0)
+    per_prime = profiled_traffic("compact_kernel_list_1e12.json", "dram_bytes_per_listed_prime")
+    return {
+        "metric": "listed primes/s", "value": n / statistics.mean(calls), "unit": "primes/s",
+        "workload": "the uint64 primes of [1e12, 1e12 + 2e10) into a device buffer (sieve_range, list mode)",
+        "primes": n, "ms_per_call": 1e3 * statistics.mean(calls),
+        "tile_kernel_ms": 1e3 * sieve_s, "compaction_ms": 1e3 * compact_s,
+        "roofline": {"bound": "hbm", "kernel": "compact_kernel", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": per_prime * n if per_prime else None,
+                     "algorithmic_bytes": alg_bytes,
+                     "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json)" if peaks.get("hbm_gbs")
+                     else "fallback 6.8 TB/s"},
+        "l2": "output (5.8 GB) exceeds L2; no flush",
+    }
+
+
 def serving_leg(rates=(1000, 3000, 10000, 30000, 100000), seconds: float = 1.0, max_n: int = 40000,
                 naive_rates: int = 2) -> dict:
     """Open-loop Poisson request streams (seed 1: lo log-uniform in [1e6, 1e18],
@@ -530,9 +589,11 @@ def run_gpu(args):
     peak = props.multi_processor_count * atom_cf * sm_max * 1e6 / 1e9
     traffic = profiled_traffic("range_tiles_count_1e12.json")
 
-    batch = serving = None
+    batch = serving = listing = None
     if world == 1 and not args.no_batch:
         batch = batch_leg(args.steps, args.warmup)
+    if world == 1 and not args.no_list:
+        listing = list_leg(args.steps, args.warmup)
     if world == 1 and not args.no_serving:
         serving = serving_leg()
 
@@ -567,6 +628,7 @@ def run_gpu(args):
                 "d2h_bytes_per_step": 8 * nb + 16},
         "gpu_launches": launches,
         "batch": batch,
+        "list": listing,
         "serving": serving,
         "clocks": clk,
         "wall_s_timed": wall,

@@ -344,6 +344,31 @@ int sieve_range_list_noalloc(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t 
  * and synchronises it.  Errors: INVALID, CUDA, OOM. */
 int sieve_measure_smem_atomics(int device, double *conflict_free, double *random_banks);
 
+/* ------------------------------------------------------------- phase timing */
+
+/* Device time of the phases of the last single-range call on this context
+ * that reached the tile kernel (sieve_count, sieve_primes, sieve_primes_u32,
+ * sieve_range, sieve_segment_counts), measured with CUDA events on the
+ * context's stream
+ * while phase timing is enabled (it is off by default; the events cost a few
+ * microseconds per call).  The paper has no counterpart: this backs the
+ * roofline figures of the tile kernel and the list compaction. */
+typedef struct {
+  double sieve_ms;    /* the tile kernel: strikes, count, bitmap write-out in list mode */
+  double scan_ms;     /* list mode: the scan of per-tile counts (0 otherwise) */
+  double compact_ms;  /* list mode: the compaction kernel (0 otherwise) */
+  uint64_t tiles;     /* tiles the tile kernel sieved */
+  uint64_t tile_len;  /* indices per residue class per tile */
+  uint64_t listed;    /* list mode: primes the compaction wrote */
+} sieve_phase_times;
+
+/* enable != 0 turns phase timing on (creating the events), 0 turns it off.
+ * Errors: INVALID (NULL ctx), CUDA. */
+int sieve_set_phase_timing(sieve_ctx *ctx, int enable);
+/* Waits for the last call's recorded events and fills *out; phases the call
+ * did not run read 0.  INVALID if ctx or out is NULL or timing is off. */
+int sieve_get_phase_times(sieve_ctx *ctx, sieve_phase_times *out);
+
 /* ------------------------------------------------------------- table 1 */
 
 /* Host evaluation of the start-index routine the kernels run (Section 3,

@@ -65,6 +65,11 @@ class ServerConfig(ctypes.Structure):
                 ("max_queue", ctypes.c_size_t), ("batch_scratch_bytes", ctypes.c_size_t)]
 
 
+class PhaseTimes(ctypes.Structure):
+    _fields_ = [("sieve_ms", ctypes.c_double), ("scan_ms", ctypes.c_double), ("compact_ms", ctypes.c_double),
+                ("tiles", ctypes.c_uint64), ("tile_len", ctypes.c_uint64), ("listed", ctypes.c_uint64)]
+
+
 class ServerStats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64), ("batches", ctypes.c_uint64),
                 ("overlapped_batches", ctypes.c_uint64), ("queued", ctypes.c_uint64),
@@ -113,6 +118,8 @@ SIGNATURES = {
     "sieve_server_get_stats": (_i, [_p, ctypes.POINTER(ServerStats), _i]),
     "sieve_server_stop": (None, [_p]),
     "sieve_measure_smem_atomics": (_i, [_i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "sieve_set_phase_timing": (_i, [_p, _i]),
+    "sieve_get_phase_times": (_i, [_p, _p]),
     "sieve_next": (_i, [_p, _u64, _sz, _p, ctypes.POINTER(_sz), _u]),
 }
 
@@ -251,6 +258,17 @@ class Sieve:
         for k, v in kw.items():
             setattr(o, k, int(v))
         _check(self._lib.sieve_set_options(self._h, ctypes.byref(o)), "sieve_set_options")
+
+    def set_phase_timing(self, enable: bool = True) -> None:
+        """Turn per-phase CUDA-event timing of single-range calls on or off."""
+        _check(self._lib.sieve_set_phase_timing(self._h, 1 if enable else 0), "sieve_set_phase_timing")
+
+    def phase_times(self) -> dict:
+        """Device times (ms) of the last single-range call's tile kernel, scan
+        and compaction, with its tile count, tile length and listed primes."""
+        t = PhaseTimes()
+        _check(self._lib.sieve_get_phase_times(self._h, ctypes.byref(t)), "sieve_get_phase_times")
+        return {k: getattr(t, k) for k, _ in PhaseTimes._fields_}
 
     def base_table(self) -> tuple[int, int, int]:
         lim = _u64(0)

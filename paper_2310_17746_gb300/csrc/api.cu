@@ -218,6 +218,8 @@ static void free_ctx(sieve_ctx *c) {
   cudaFree(c->d_scratch);
   cudaFree(c->d_stage);
   if (c->h_acc) cudaFreeHost(c->h_acc);
+  for (cudaEvent_t &e : c->ph_ev)
+    if (e) cudaEventDestroy(e);
   delete c;
 }
 
@@ -522,6 +524,42 @@ extern "C" int sieve_base_table(const sieve_ctx *ctx, uint64_t *limit, uint64_t 
 }
 
 extern "C" uint64_t sieve_launch_count(const sieve_ctx *ctx) { return ctx ? ctx->launches.load() : 0; }
+
+extern "C" int sieve_set_phase_timing(sieve_ctx *ctx, int enable) {
+  if (!ctx) {
+    set_error("sieve_set_phase_timing: NULL context");
+    return SIEVE_ERR_INVALID;
+  }
+  if (enable) {
+    SIEVE_CUDA_TRY(cudaSetDevice(ctx->device));
+    for (cudaEvent_t &e : ctx->ph_ev)
+      if (!e) SIEVE_CUDA_TRY(cudaEventCreate(&e));
+  }
+  ctx->phase_timing = enable != 0;
+  ctx->ph_recorded = 0;
+  ctx->ph = sieve_phase_times{};
+  return SIEVE_OK;
+}
+
+extern "C" int sieve_get_phase_times(sieve_ctx *ctx, sieve_phase_times *out) {
+  if (!ctx || !out || !ctx->phase_timing) {
+    set_error("sieve_get_phase_times: NULL argument or phase timing off");
+    return SIEVE_ERR_INVALID;
+  }
+  sieve_phase_times t = ctx->ph;
+  const uint32_t r = ctx->ph_recorded;
+  const int from[3] = {0, 1, 3}, to[3] = {1, 2, 4};
+  double *dst[3] = {&t.sieve_ms, &t.scan_ms, &t.compact_ms};
+  for (int i = 0; i < 3; i++) {
+    if ((r & (1u << from[i])) == 0 || (r & (1u << to[i])) == 0) continue;
+    float ms = 0.0f;
+    SIEVE_CUDA_TRY(cudaEventSynchronize(ctx->ph_ev[to[i]]));
+    SIEVE_CUDA_TRY(cudaEventElapsedTime(&ms, ctx->ph_ev[from[i]], ctx->ph_ev[to[i]]));
+    *dst[i] = ms;
+  }
+  *out = t;
+  return SIEVE_OK;
+}
 
 extern "C" const char *sieve_last_error(void) { return g_err; }
 

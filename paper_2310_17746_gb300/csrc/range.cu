@@ -311,6 +311,12 @@ static uint32_t floor_pow2(uint64_t x) {
   return r;
 }
 
+// Records phase-timing event i on the context's stream when timing is on.
+static void phase_event(sieve_ctx *ctx, int i) {
+  if (!ctx->phase_timing) return;
+  if (cudaEventRecord(ctx->ph_ev[i], ctx->stream) == cudaSuccess) ctx->ph_recorded |= 1u << i;
+}
+
 static uint32_t log2u(uint32_t x) {
   uint32_t r = 0;
   while ((1u << r) < x) r++;
@@ -475,10 +481,18 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
     p.bitmap = (uint2 *)(scr + off_bitmap);
   }
 
+  if (ctx->phase_timing) {
+    ctx->ph = sieve_phase_times{};
+    ctx->ph.tiles = ntiles;
+    ctx->ph.tile_len = L;
+    ctx->ph_recorded = 0;
+    phase_event(ctx, 0);
+  }
   if (ntiles) {
     rc = dispatch_launch(ctx, threads, p, req.list != 0, grid, smem);
     if (rc != SIEVE_OK) return rc;
   }
+  phase_event(ctx, 1);
 
   if (!req.list) {
     if (!dev_out) {
@@ -502,6 +516,7 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
     scan_tile_counts_kernel<1024><<<1, 1024, 0, st>>>(p.tile_counts, offsets, ntiles);
     ctx->launches++;
     SIEVE_CUDA_TRY(cudaGetLastError());
+    phase_event(ctx, 2);
     SIEVE_CUDA_TRY(cudaMemcpyAsync(ctx->h_acc + 2, offsets + ntiles, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
   } else {
     ctx->h_acc[2] = 0;
@@ -546,12 +561,15 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
   cp.cap = req.cap;
   const size_t csmem = compact_smem_bytes(L);
   const int cgrid = (int)std::min<uint64_t>(ntiles, (uint64_t)ctx->num_sms * 4);
+  phase_event(ctx, 3);
   if (req.out_bytes == 4)
     compact_kernel<kCompactBlock, uint32_t><<<cgrid, kCompactBlock, csmem, st>>>(cp);
   else
     compact_kernel<kCompactBlock, uint64_t><<<cgrid, kCompactBlock, csmem, st>>>(cp);
   ctx->launches++;
   SIEVE_CUDA_TRY(cudaGetLastError());
+  phase_event(ctx, 4);
+  if (ctx->phase_timing) ctx->ph.listed = total;
   if (!dev_out)
     SIEVE_CUDA_TRY(cudaMemcpyAsync(req.out, dst, (size_t)total * req.out_bytes, cudaMemcpyDeviceToHost, st));
   SIEVE_CUDA_TRY(cudaStreamSynchronize(st));

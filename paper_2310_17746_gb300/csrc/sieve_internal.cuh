@@ -303,6 +303,13 @@ struct sieve_ctx {
   size_t stage_bytes = 0;
   // pinned host staging
   unsigned long long *h_acc = nullptr;
+  // phase timing of single-range calls (sieve_set_phase_timing): events
+  // around the tile kernel (0, 1), after the scan (2; it starts at 1), and
+  // around the compaction (3, 4)
+  bool phase_timing = false;
+  cudaEvent_t ph_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  uint32_t ph_recorded = 0;  // bit i: ph_ev[i] recorded by the last call
+  sieve_phase_times ph{};
 };
 
 namespace sieve {

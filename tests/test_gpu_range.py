@@ -169,3 +169,31 @@ def test_errors(sv):
         sv.set_options(tile_bits=1 << 20)  # 256 KB of bitmaps do not fit in shared memory
     r = sv.range_count(77, 77)
     assert (r.count, r.checksum) == (0, 0)
+
+
+def test_phase_timing(sv):
+    """Per-phase CUDA-event timing of a range call: the tile kernel, scan and
+    compaction times are positive in list mode, the listed count matches, and
+    timing changes no result."""
+    import torch
+
+    lo, hi = 10**9, 10**9 + 3 * 10**7
+    with binding.Sieve(hi) as sv:  # a context of its own: timing is off by default
+        want = sv.range_count(lo, hi)
+        with pytest.raises(binding.SieveError):
+            sv.phase_times()
+        sv.set_phase_timing(True)
+        got = sv.range_count(lo, hi)
+        t = sv.phase_times()
+        assert (got.count, got.checksum) == (want.count, want.checksum)
+        assert t["sieve_ms"] > 0 and t["scan_ms"] == 0 and t["compact_ms"] == 0 and t["listed"] == 0
+        assert t["tiles"] * t["tile_len"] >= (hi - lo) // 6
+        out = torch.zeros(want.count, dtype=torch.int64, device="cuda")
+        n = sv.range_list(lo, hi, out=out)
+        t = sv.phase_times()
+        assert n == want.count == t["listed"]
+        assert t["sieve_ms"] > 0 and t["scan_ms"] > 0 and t["compact_ms"] > 0
+        np.testing.assert_array_equal(out.cpu().numpy().astype(np.uint64), oracle.list_range(lo, hi))
+        sv.set_phase_timing(False)
+        with pytest.raises(binding.SieveError):
+            sv.phase_times()
