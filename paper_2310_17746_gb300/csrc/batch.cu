@@ -663,16 +663,23 @@ int batch_plan(BatchRunner &r, const uint64_t *lo, const uint64_t *hi, const uin
     bq.i_split = i_split;
     // Primes above the tile length hit a tile at most twice.  Strips locate
     // them once per query and clear each hit with a global atomic; tiles
-    // locate them once per tile.  Strips are taken when they cost less.
-    uint32_t i_mid = host_prime_count_le_table(table, L);
-    if (i_mid < i_first) i_mid = i_first;
+    // locate them once per tile.  A prime p costs ntiles evaluations on the
+    // tiles and one evaluation plus about 2 span / p atomics as a strip, so
+    // the tiles keep every prime below p* = gcost 2 span / (kCostPrime
+    // (ntiles - 1)) (about 8 L), and strips take the primes above it when
+    // they cost less in total.
     QueryPlanInfo &qi = info[i];
+    qi.gcost = (double)span / 4.0 > kL2Bitmap ? 4.0 * kCostGlobal : kCostGlobal;
+    const double pstar =
+        ntiles > 1 ? qi.gcost * 2.0 * (double)span / (kCostPrime * (double)(ntiles - 1)) : (double)L;
+    const uint64_t p_split = std::max<uint64_t>(L, (uint64_t)std::min(pstar, (double)s));
+    uint32_t i_mid = host_prime_count_le_table(table, p_split);
+    if (i_mid < i_first) i_mid = i_first;
     qi.np = np;
     qi.i_mid = i_mid;
     const double pm = (double)P[std::min(i_mid, table.nprimes - 1)];
     const double hits = np > i_mid ? 2.0 * (double)span * (lnln((double)P[np - 1]) - lnln(pm)) : 0.0;
     const double large = np > i_mid ? (double)(np - i_mid) : 0.0;
-    qi.gcost = (double)span / 4.0 > kL2Bitmap ? 4.0 * kCostGlobal : kCostGlobal;
     qi.strips = ntiles >= 2 && span < (1ull << 31) && np > i_mid &&
                 kCostPrime * large + qi.gcost * hits < kCostPrime * large * (double)ntiles;
     const uint32_t t_end = qi.strips ? i_mid : std::max(np, i_first);
