@@ -146,8 +146,16 @@ __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK > 0 ? 1024 / BLOCK : 1)) 
       const uint64_t stream = l2_policy_evict_first(), keep = l2_policy_evict_last();
       for (uint32_t i = it.i0 + threadIdx.x; i < it.i1; i += BLOCK) {
         const uint32_t P = ld_hint_u32(a.primes + i, stream);
+        const uint64_t m = ld_hint_u64(a.magic + i, stream);
         uint64_t k1, k5;
-        tile_starts(Bq, P, ld_hint_u64(a.magic + i, stream), k1, k5);
+        if ((uint64_t)P * P <= Bq && P < 0x80000000u) {  // the inverse-of-6 start (= Table 1's)
+          uint32_t i1, i5;
+          starts_from_inverse(qd.k_begin, P, m, inverse6_constants(P), i1, i5);
+          k1 = i1;
+          k5 = i5;
+        } else {
+          tile_starts(Bq, P, m, k1, k5);
+        }
         for (uint64_t k = k1; k < span; k += P) strike_merged(gq, k, 0, logL, logW, keep);
         for (uint64_t k = k5; k < span; k += P) strike_merged(gq, k, 1, logL, logW, keep);
       }

@@ -223,20 +223,23 @@ __host__ __device__ __forceinline__ bool tile_starts_within(uint64_t B, uint32_t
   return true;
 }
 
-// The same start indices from a per-prime inverse of 6.  Class r's index k
-// holds value 6 (K0 + k) + r, which P divides iff K0 + k = -r / 6 (mod P);
-// so with c_r = (-r / 6) mod P (a per-prime constant) the first such k >= 0
-// is (c_r - K0 mod P) mod P.  This equals the Table 1 start whenever P^2 <=
-// 6 K0 (no clamp; the start lies below P), and costs one invariant-division
-// remainder and a few 32-bit operations instead of the table's case split.
-// 6^{-1} mod P is (P + 1) / 6 for P = 5 (mod 6) and (5 P + 1) / 6 for P = 1.
+// The same start indices from the inverse of 6.  Class r's index k holds
+// value 6 (K0 + k) + r, which P divides iff K0 + k = -r / 6 (mod P); so with
+// c_r = (-r / 6) mod P the first such k >= 0 is (c_r - K0 mod P) mod P.  The
+// base table keeps (c_1, c_5) per prime for the tiles' one-lane band (a load
+// is cheaper there than the arithmetic below, measured); the strips, which
+// stream the table from DRAM, compute them.  This
+// equals the Table 1 start whenever P^2 <= 6 K0 (no clamp; the start lies
+// below P), and costs one invariant-division remainder and a few 32-bit
+// operations instead of the table's case split.  The constants have a closed
+// form in R = floor(P / 6): 6^{-1} mod P is (P + 1) / 6 = R + 1 for P = 6R + 5
+// and (5 P + 1) / 6 = 5R + 1 for P = 6R + 1, so
+//   P = 6R + 1:  c_1 = R,       c_5 = 5R
+//   P = 6R + 5:  c_1 = 5R + 4,  c_5 = R
+// (P >= 5, P % 6 in {1, 5}).
 __host__ __device__ __forceinline__ uint2 inverse6_constants(uint32_t P) {
-  if (P < 5) return make_uint2(0, 0);
-  const uint64_t inv6 = P % 6u == 5u ? ((uint64_t)P + 1) / 6 : (5ull * P + 1) / 6;
-  const uint64_t c1 = P - inv6;                  // -1/6 mod P (inv6 in [1, P))
-  const uint64_t i5 = (5 * inv6) % P;            // 5/6 mod P
-  const uint64_t c5 = i5 == 0 ? 0 : P - i5;      // -5/6 mod P
-  return make_uint2((uint32_t)c1, (uint32_t)c5);
+  const uint32_t R = P / 6u;
+  return P - 6u * R == 1u ? make_uint2(R, 5u * R) : make_uint2(5u * R + 4u, R);
 }
 
 // k1 / k5 = (c - K0 mod P) mod P for P < 2^31 (m = reciprocal64(P)).
