@@ -206,3 +206,32 @@ def test_batch_single_huge_tile_is_split(sv):
         cnt, off, vals = sv.range_batch([lo], [hi], [m])
         _check_against_oracle(np.array([lo], np.uint64), np.array([hi], np.uint64), np.array([m], np.uint8),
                               cnt, off, vals)
+
+
+def test_batch_strip_primes_squared_inside_queries(sv):
+    """Queries centred on P^2 for primes P far above the break-even prime of
+    the strips (small batch tiles): such a strip prime starts at its square
+    (the clamp path of the start computation), the others from the inverse of
+    6.  Both modes, against the oracle."""
+    opts = sv.options()
+    try:
+        sv.set_options(batch_tile_bits=1 << 12, block_threads=512, chunk_primes=1024)
+        lo, hi, mode = [], [], []
+        for near in (10**6, 2 * 10**6, 3_162_000):
+            p = int(oracle.list_range(near, near + 200)[0])
+            sq = p * p
+            for half in (60_000, 300_000):
+                for m in (0, 1):
+                    lo.append(sq - half)
+                    hi.append(sq + half + 1)
+                    mode.append(m)
+            lo.append(sq)  # the square is the query's first value
+            hi.append(sq + 200_000)
+            mode.append(1)
+        lo = np.array(lo, dtype=np.uint64)
+        hi = np.array(hi, dtype=np.uint64)
+        mode = np.array(mode, dtype=np.uint8)
+        cnt, off, vals = sv.range_batch(lo, hi, mode)
+        _check_against_oracle(lo, hi, mode, cnt, off, vals)
+    finally:
+        _restore(sv, opts)
