@@ -384,8 +384,10 @@ int sieve_table1_start(uint64_t B, uint64_t M, uint32_t P, int64_t *id1, int64_t
  * (M = B), from a per-prime inverse of 6 instead of Table 1's case split.
  * Index k of class r stands for 6 (B / 6 + k) + r, which P divides iff
  * B / 6 + k = -r / 6 (mod P), so the first such k is
- * (c_r - (B / 6) mod P) mod P with c_r = (-r / 6) mod P.  The one-lane
- * strike band uses it whenever P^2 <= B (then it equals Table 1's start).
+ * (c_r - (B / 6) mod P) mod P with c_r = (-r / 6) mod P (in closed form:
+ * with R = floor(P / 6), (c_1, c_5) = (R, 5R) for P = 6R + 1 and (5R + 4, R)
+ * for P = 6R + 5).  The tiles' one-lane strike band and the batch strips use
+ * it whenever P^2 <= B (then it equals Table 1's start).
  * Requires B % 6 == 0, 5 <= P < 2^31, P % 6 in {1, 5} and P^2 <= B, else
  * INVALID. */
 int sieve_inverse6_start(uint64_t B, uint32_t P, uint32_t *id1, uint32_t *id5);
