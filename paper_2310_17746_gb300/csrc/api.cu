@@ -229,7 +229,7 @@ static sieve_options default_options() {
   o.tile_bits = 1u << 19;
   o.block_threads = 1024;
   o.ctas_per_sm = 0;
-  o.group_hits = 4;       // measured best with presieve_groups 7 at [2, 1e12] (183 vs 188 ms for 8 / 5)
+  o.group_hits = 5;       // measured best with presieve_groups 7 at [2, 1e12] (181.4 ms; 4: 182.1, 8: 184.1)
   o.presieve_groups = 7;  // patterns to 109
   o.batch_tile_bits = 1u << 18;
   o.chunk_primes = 1u << 15;
