@@ -79,16 +79,32 @@ __device__ __forceinline__ void emit_tile(const BatchArena &a, const BatchQuery 
   uint2 *bm = list ? a.list_bm + qd.bitmap_off + (uint64_t)t * W : nullptr;
   // 32-bit per-thread sums (as in the range kernel): class counts, the
   // word-weighted count and the bit-position sum; the 64-bit checksum once
-  uint32_t c1 = 0, c5 = 0, sw = 0, bs = 0;
-  for (uint32_t w = threadIdx.x; w < W; w += BLOCK) {
-    const uint32_t x = s1[w], y = s5[w];
+  uint32_t c1 = 0, c5 = 0, sw = 0;
+  BitPlanes planes;  // the bit-position sum, four word pairs at a time
+  auto pair = [&](uint32_t w, uint32_t x, uint32_t y) {
     if (list) bm[w] = make_uint2(x, y);
     const uint32_t cx = __popc(x), cy = __popc(y);
     c1 += cx;
     c5 += cy;
     sw += w * (cx + cy);
-    bs += bit_index_sum(x) + bit_index_sum(y);
+  };
+  uint32_t w = threadIdx.x;
+  for (; w + 3 * BLOCK < W; w += 4 * BLOCK) {
+    const uint32_t x0 = s1[w], y0 = s5[w], x1 = s1[w + BLOCK], y1 = s5[w + BLOCK];
+    const uint32_t x2 = s1[w + 2 * BLOCK], y2 = s5[w + 2 * BLOCK], x3 = s1[w + 3 * BLOCK], y3 = s5[w + 3 * BLOCK];
+    pair(w, x0, y0);
+    pair(w + BLOCK, x1, y1);
+    pair(w + 2 * BLOCK, x2, y2);
+    pair(w + 3 * BLOCK, x3, y3);
+    planes.add8(x0, y0, x1, y1, x2, y2, x3, y3);
   }
+  for (; w < W; w += BLOCK) {
+    const uint32_t x = s1[w], y = s5[w];
+    pair(w, x, y);
+    planes.add1(x);
+    planes.add1(y);
+  }
+  const uint32_t bs = planes.index_sum();
   uint64_t cnt = (uint64_t)c1 + c5, unused = 0;
   uint64_t sum = (uint64_t)c1 * (6 * K0 + 1) + (uint64_t)c5 * (6 * K0 + 5) + 6ull * sw + 6ull * W * bs;
   block_sum3<BLOCK>(cnt, sum, unused, red);

@@ -106,20 +106,36 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
     // so a thread accumulates, in 32 bits, the class counts c1 / c5, the
     // word-weighted count sw and the bit-position sum bs of its words
     // (sw < 2^15 * 64 * (W / BLOCK) < 2^32), and forms the 64-bit sum once.
-    uint32_t c1 = 0, c5 = 0, sw = 0, bs = 0, below32 = 0;
+    uint32_t c1 = 0, c5 = 0, sw = 0, below32 = 0;
+    BitPlanes planes;  // the bit-position sum, four word pairs at a time
     const int has_b = sh_has_boundary;
     const int64_t t1 = has_b ? sh_t1 : 0, t5 = has_b ? sh_t5 : 0;
-    for (uint32_t w = threadIdx.x; w < W; w += BLOCK) {
-      const uint32_t a = s1[w], b = s5[w];
+    auto pair = [&](uint32_t w, uint32_t a, uint32_t b) {
       if (LIST) p.bitmap[(uint64_t)t * W + w] = make_uint2(a, b);
       const uint32_t ca = __popc(a), cb = __popc(b);
       c1 += ca;
       c5 += cb;
       sw += w * (ca + cb);
-      bs += bit_index_sum(a) + bit_index_sum(b);
       if (has_b)
         below32 += __popc(a & below_mask(t1, w, tg.logW, W)) + __popc(b & below_mask(t5, w, tg.logW, W));
+    };
+    uint32_t w = threadIdx.x;
+    for (; w + 3 * BLOCK < W; w += 4 * BLOCK) {
+      const uint32_t a0 = s1[w], b0 = s5[w], a1 = s1[w + BLOCK], b1 = s5[w + BLOCK];
+      const uint32_t a2 = s1[w + 2 * BLOCK], b2 = s5[w + 2 * BLOCK], a3 = s1[w + 3 * BLOCK], b3 = s5[w + 3 * BLOCK];
+      pair(w, a0, b0);
+      pair(w + BLOCK, a1, b1);
+      pair(w + 2 * BLOCK, a2, b2);
+      pair(w + 3 * BLOCK, a3, b3);
+      planes.add8(a0, b0, a1, b1, a2, b2, a3, b3);
     }
+    for (; w < W; w += BLOCK) {
+      const uint32_t a = s1[w], b = s5[w];
+      pair(w, a, b);
+      planes.add1(a);
+      planes.add1(b);
+    }
+    const uint32_t bs = planes.index_sum();
     uint64_t cnt = (uint64_t)c1 + c5, below = below32;
     uint64_t sum = (uint64_t)c1 * (6 * K0 + 1) + (uint64_t)c5 * (6 * K0 + 5) + 6ull * sw + 6ull * W * bs;
     block_sum3<BLOCK>(cnt, sum, below, red);

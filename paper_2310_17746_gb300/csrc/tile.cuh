@@ -281,6 +281,51 @@ __device__ __forceinline__ uint32_t bit_index_sum(uint32_t x) {
          (__popc(x & 0xFF00FF00u) << 3) + (__popc(x & 0xFFFF0000u) << 4);
 }
 
+// Carry-save bit-plane counters (Harley-Seal): after words x_1 .. x_n (n <
+// 256) are added, bit b of plane k is bit k of the number of words with bit
+// b set, so index_sum() = sum over all set bits of their positions b = the
+// sum of bit_index_sum(x_i).  Eight words cost seven full adders (two
+// three-input logic operations each) and a ripple of the top carry, about
+// three operations per word against fourteen for bit_index_sum.
+struct BitPlanes {
+  uint32_t p[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // a + b + c = 2 h + l, bitwise
+  __device__ __forceinline__ static void csa(uint32_t &h, uint32_t &l, uint32_t a, uint32_t b, uint32_t c) {
+    const uint32_t u = a ^ b;
+    h = (a & b) | (u & c);
+    l = u ^ c;
+  }
+  __device__ __forceinline__ void carry_from(int k, uint32_t x) {
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      if (j >= k) {
+        const uint32_t c = p[j] & x;
+        p[j] ^= x;
+        x = c;
+      }
+    }
+  }
+  __device__ __forceinline__ void add1(uint32_t x) { carry_from(0, x); }
+  __device__ __forceinline__ void add8(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, uint32_t w4,
+                                       uint32_t w5, uint32_t w6, uint32_t w7) {
+    uint32_t ta, tb, tc, td, fa, fb, e;
+    csa(ta, p[0], p[0], w0, w1);
+    csa(tb, p[0], p[0], w2, w3);
+    csa(tc, p[0], p[0], w4, w5);
+    csa(td, p[0], p[0], w6, w7);
+    csa(fa, p[1], p[1], ta, tb);
+    csa(fb, p[1], p[1], tc, td);
+    csa(e, p[2], p[2], fa, fb);
+    carry_from(3, e);
+  }
+  __device__ __forceinline__ uint32_t index_sum() const {
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) s += bit_index_sum(p[k]) << k;
+    return s;
+  }
+};
+
 template <int BLOCK>
 __device__ __forceinline__ void block_sum3(uint64_t &a, uint64_t &b, uint64_t &c, uint64_t *red) {
   constexpr int NWARPS = BLOCK / 32;
