@@ -216,8 +216,7 @@ __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK > 0 ? 1024 / BLOCK : 1)) 
         if (y != 0xFFFFFFFFu) red_and_hint(g5 + w, y, keep);
       }
     } else {
-      fixup_tile<BLOCK>(s1, s5, tg, K0, valid_range(qd.lo, qd.hi, B, tg.len), npat);
-      __syncthreads();
+      fixup_tile<BLOCK>(s1, s5, tg, K0, valid_range(qd.lo, qd.hi, B, tg.len), npat);  // ends with a barrier if needed
       emit_tile<BLOCK>(a, qd, it.q, it.t, s1, s5, W, logW, K0, red);
     }
     __syncthreads();  // shared memory and sh_idx are reused by the next item
@@ -254,8 +253,7 @@ __global__ void __launch_bounds__(BLOCK) batch_finish_kernel(const BatchArena a)
       s5[w] = g5[w];
     }
     __syncthreads();
-    fixup_tile<BLOCK>(s1, s5, tg, K0, valid_range(qd.lo, qd.hi, 6 * K0, tg.len), npat);
-    __syncthreads();
+    fixup_tile<BLOCK>(s1, s5, tg, K0, valid_range(qd.lo, qd.hi, 6 * K0, tg.len), npat);  // ends with a barrier if needed
     emit_tile<BLOCK>(a, qd, qt.x, qt.y, s1, s5, W, logW, K0, red);
     __syncthreads();
   }

@@ -97,8 +97,7 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
     __syncthreads();
 
     const ValidRange v = valid_range(p.lo, p.hi, B, tg.len);
-    fixup_tile<BLOCK>(s1, s5, tg, K0, v, p.npat);
-    __syncthreads();
+    fixup_tile<BLOCK>(s1, s5, tg, K0, v, p.npat);  // ends with a barrier when it changes the tile
 
     // popcount, checksum, and the count below the segment boundary (if any).
     // Word w holds indices w + b W: their values sum to

@@ -251,7 +251,15 @@ __device__ __forceinline__ ValidRange valid_range(uint64_t lo, uint64_t hi, uint
 template <int BLOCK>
 __device__ __forceinline__ void fixup_tile(uint32_t *s1, uint32_t *s5, const TileGeom &tg, uint64_t K0,
                                            const ValidRange &v, int npat) {
-  if (threadIdx.x == 0 && 6 * K0 <= 131) {
+  // Nothing to fix in a tile above the presieved primes that lies inside the
+  // range (most tiles): return at once, without the barriers.  The condition
+  // is the same for every thread of the block.  Otherwise the tile is ready
+  // when this returns (it ends with a barrier).
+  const int64_t full = 32 * (int64_t)tg.W;
+  const bool small = 6 * K0 <= 131;
+  const bool edge = v.kl1 > 0 || v.kl5 > 0 || v.kh1 < full || v.kh5 < full;
+  if (!small && !edge) return;
+  if (threadIdx.x == 0 && small) {
     if (K0 == 0) s1[0] &= ~1u;  // 1 is not a prime (index 0: word 0, bit 0)
     for (int g = 0; g < npat; g++) {
       for (int q = 0; q < 6; q++) {
@@ -266,13 +274,13 @@ __device__ __forceinline__ void fixup_tile(uint32_t *s1, uint32_t *s5, const Til
     }
   }
   __syncthreads();
-  const int64_t full = 32 * (int64_t)tg.W;
-  if (v.kl1 > 0 || v.kl5 > 0 || v.kh1 < full || v.kh5 < full) {
+  if (edge) {
     for (uint32_t w = threadIdx.x; w < tg.W; w += BLOCK) {
       s1[w] &= below_mask(v.kh1, w, tg.logW, tg.W) & ~below_mask(v.kl1, w, tg.logW, tg.W);
       s5[w] &= below_mask(v.kh5, w, tg.logW, tg.W) & ~below_mask(v.kl5, w, tg.logW, tg.W);
     }
   }
+  __syncthreads();
 }
 
 // Sum over the set bits b of x of b.
