@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK > 0 ? 1024 / BLOCK : 1)) 
     const PatternSetDev *ps = a.psets + logW;
     presieve_copy<BLOCK>(s1, s5, tg, K0, ps->d, ps->pd, npat);
     const uint32_t split = qd.i_split < it.i1 ? qd.i_split : it.i1;
-    warp_band_starts<BLOCK>(starts, B, tg.len, a.primes, a.magic, it.i0, split);
+    warp_band_starts<BLOCK>(starts, B, tg.len, a.primes, a.magic, a.cinv, it.i0, split);
     __syncthreads();
     strike_primes<BLOCK>(s1, s5, B, tg, a.primes, a.magic, a.cinv, starts, it.i0, split, sh_np, &sh_next);
     __syncthreads();

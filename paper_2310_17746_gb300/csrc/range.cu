@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
   __shared__ int sh_has_boundary;
   __shared__ uint64_t red[3 * NWARPS];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t np_prev = 0;  // warp 0: the previous tile's prime count
 
   for (uint32_t t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
     const uint64_t K0 = p.k_begin + (uint64_t)t * p.L;
@@ -68,9 +69,14 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
     const uint64_t vend = tile_end < p.hi ? tile_end : p.hi;
 
     if (warp == 0) {
-      // base primes needed: P <= isqrt(vend - 1)
+      // base primes needed: P <= isqrt(vend - 1).  A CTA's tiles go up, so
+      // the count of the previous tile stays right unless the next prime
+      // joins (then search again).
       const uint64_t s = vend >= 2 ? isqrt_dev(vend - 1) : 0;
-      const uint32_t np = warp_count_le(p.primes, p.nprimes, s);
+      const bool grows = np_prev < p.nprimes && (uint64_t)__ldg(p.primes + np_prev) <= s;
+      const bool shrinks = np_prev > 0 && (uint64_t)__ldg(p.primes + np_prev - 1) > s;
+      if (grows || shrinks) np_prev = warp_count_le(p.primes, p.nprimes, s);
+      const uint32_t np = np_prev;
       if (lane == 0) {
         sh_np = np;
         sh_next = p.i_first;
@@ -90,7 +96,7 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
       }
     }
     presieve_copy<BLOCK>(s1, s5, tg, K0, p.sliced, p.pd, p.npat);
-    warp_band_starts<BLOCK>(starts, B, tg.len, p.primes, p.magic, p.i_first, p.i_split);
+    warp_band_starts<BLOCK>(starts, B, tg.len, p.primes, p.magic, p.cinv, p.i_first, p.i_split);
     __syncthreads();
 
     strike_primes<BLOCK>(s1, s5, B, tg, p.primes, p.magic, p.cinv, starts, p.i_first, p.i_split, sh_np, &sh_next);

@@ -117,11 +117,20 @@ __device__ __forceinline__ void strike(uint32_t *s, uint32_t k, uint32_t step, u
 template <int BLOCK>
 __device__ __forceinline__ void warp_band_starts(uint2 *starts, uint64_t B, uint32_t len,
                                                  const uint32_t *__restrict__ primes,
-                                                 const uint64_t *__restrict__ magic, uint32_t i_first,
+                                                 const uint64_t *__restrict__ magic,
+                                                 const uint2 *__restrict__ cinv, uint32_t i_first,
                                                  uint32_t i_split) {
   for (uint32_t i = i_first + threadIdx.x; i < i_split; i += BLOCK) {
+    const uint32_t P = __ldg(primes + i);
     uint64_t k1, k5;
-    tile_starts(B, __ldg(primes + i), __ldg(magic + i), k1, k5);
+    if ((uint64_t)P * P <= B && P < 0x80000000u) {  // the inverse-of-6 start (= Table 1's)
+      uint32_t a1, a5;
+      starts_from_inverse(B / 6, P, __ldg(magic + i), __ldg(cinv + i), a1, a5);
+      k1 = a1;
+      k5 = a5;
+    } else {
+      tile_starts(B, P, __ldg(magic + i), k1, k5);
+    }
     starts[i - i_first] = make_uint2(k1 < len ? (uint32_t)k1 : len, k5 < len ? (uint32_t)k5 : len);
   }
 }
@@ -329,7 +338,8 @@ struct BitPlanes {
   __device__ __forceinline__ uint32_t index_sum() const {
     uint32_t s = 0;
 #pragma unroll
-    for (int k = 0; k < 8; k++) s += bit_index_sum(p[k]) << k;
+    for (int k = 0; k < 8; k++)
+      if (p[k]) s += bit_index_sum(p[k]) << k;  // the top planes are mostly empty
     return s;
   }
 };
