@@ -128,7 +128,7 @@ template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK > 0 ? 1024 / BLOCK : 1)) batch_sieve_kernel(const BatchArena a) {
   constexpr int NWARPS = BLOCK / 32;
   extern __shared__ uint32_t smem[];
-  __shared__ uint32_t sh_idx, sh_next, sh_np;
+  __shared__ uint32_t sh_idx, sh_next, sh_np, sh_allsq;
   __shared__ uint64_t red[3 * NWARPS];
   const char *plan = (const char *)a.plan;
   const BatchHeader *hdr = (const BatchHeader *)plan;
@@ -194,8 +194,12 @@ __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK > 0 ? 1024 / BLOCK : 1)) 
       // primes this tile needs: P <= isqrt(vend - 1), within the item's range
       const uint64_t s = vend >= 2 ? isqrt_dev(vend - 1) : 0;
       const uint32_t np = warp_count_le(a.primes, it.i1, s);
+      const uint32_t npt = np > it.i0 ? np : it.i0;
+      // every needed prime is below sqrt(B) (and 2^31): no P^2 clamp in this tile
+      const uint64_t Plast = npt ? __ldg(a.primes + npt - 1) : 0;
       if (lane == 0) {
-        sh_np = np > it.i0 ? np : it.i0;
+        sh_np = npt;
+        sh_allsq = Plast * Plast <= B && Plast < 0x80000000ull;
         sh_next = it.i0;
       }
     }
@@ -204,7 +208,8 @@ __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK > 0 ? 1024 / BLOCK : 1)) 
     const uint32_t split = qd.i_split < it.i1 ? qd.i_split : it.i1;
     warp_band_starts<BLOCK>(starts, B, tg.len, a.primes, a.magic, a.cinv, it.i0, split);
     __syncthreads();
-    strike_primes<BLOCK>(s1, s5, B, tg, a.primes, a.magic, a.cinv, starts, it.i0, split, sh_np, &sh_next);
+    strike_primes<BLOCK>(s1, s5, B, tg, a.primes, a.magic, a.cinv, starts, it.i0, split, sh_np, sh_allsq != 0,
+                         &sh_next);
     __syncthreads();
     if (merged) {
       // AND the shared-memory result into the query's bitmap in global memory

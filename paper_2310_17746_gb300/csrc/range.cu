@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
   uint32_t *s1 = smem;
   uint32_t *s5 = smem + W;
   uint2 *starts = (uint2 *)(smem + 2 * W);  // warp-band start indices
-  __shared__ uint32_t sh_np, sh_next;
+  __shared__ uint32_t sh_np, sh_next, sh_allsq;
   __shared__ uint64_t sh_bin0;
   __shared__ int64_t sh_t1, sh_t5;
   __shared__ int sh_has_boundary;
@@ -77,8 +77,11 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
       const bool shrinks = np_prev > 0 && (uint64_t)__ldg(p.primes + np_prev - 1) > s;
       if (grows || shrinks) np_prev = warp_count_le(p.primes, p.nprimes, s);
       const uint32_t np = np_prev;
+      // every needed prime is below sqrt(B) (and 2^31): no P^2 clamp in this tile
+      const uint64_t Plast = np ? __ldg(p.primes + np - 1) : 0;
       if (lane == 0) {
         sh_np = np;
+        sh_allsq = Plast * Plast <= B && Plast < 0x80000000ull;
         sh_next = p.i_first;
         sh_has_boundary = 0;
         if (p.seg_width) {
@@ -99,7 +102,8 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
     warp_band_starts<BLOCK>(starts, B, tg.len, p.primes, p.magic, p.cinv, p.i_first, p.i_split);
     __syncthreads();
 
-    strike_primes<BLOCK>(s1, s5, B, tg, p.primes, p.magic, p.cinv, starts, p.i_first, p.i_split, sh_np, &sh_next);
+    strike_primes<BLOCK>(s1, s5, B, tg, p.primes, p.magic, p.cinv, starts, p.i_first, p.i_split, sh_np,
+                         sh_allsq != 0, &sh_next);
     __syncthreads();
 
     const ValidRange v = valid_range(p.lo, p.hi, B, tg.len);

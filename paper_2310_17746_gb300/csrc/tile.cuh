@@ -155,7 +155,9 @@ __device__ __forceinline__ void warp_band_starts(uint2 *starts, uint64_t B, uint
 // one at a time through a shared counter so that warps finish together; the
 // rest by one lane each, which locates the prime's first hits from its
 // inverse-of-6 constants (cinv; the Table 1 start, see starts_from_inverse)
-// or, where the P^2 clamp can apply, with Table 1 itself.  (Loading the
+// or, where the P^2 clamp can apply, with Table 1 itself (all_sq: the caller
+// knows that every prime below np has P^2 <= B and P < 2^31, so the test per
+// prime is skipped).  (Loading the
 // constants only for primes below the tile span, so that larger ones keep a
 // one-remainder miss test, was slower: the load then waits for the prime.)
 template <int BLOCK>
@@ -163,7 +165,7 @@ __device__ __forceinline__ void strike_primes(uint32_t *s1, uint32_t *s5, uint64
                                               const uint32_t *__restrict__ primes,
                                               const uint64_t *__restrict__ magic, const uint2 *__restrict__ cinv,
                                               const uint2 *starts, uint32_t i_first, uint32_t i_split, uint32_t np,
-                                              uint32_t *next) {
+                                              bool all_sq, uint32_t *next) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t split = i_split < np ? i_split : np;
   const uint32_t len = tg.len, wmask = tg.W - 1, logW = tg.logW, span6 = 6 * tg.len;
@@ -179,56 +181,68 @@ __device__ __forceinline__ void strike_primes(uint32_t *s1, uint32_t *s5, uint64
     if (k5 < len) strike(s5, k5, 32u * P, len, wmask, logW);
   }
   // one lane per prime; the next prime's table entries are loaded before the
-  // current prime is struck so that their latency overlaps the strikes
+  // current prime is struck so that their latency overlaps the strikes.  The
+  // loop is unrolled by two with the prefetched entries alternating between
+  // two register sets (fewer moves than rotating one set; measured).
   const uint64_t K0 = B / 6;
-  uint32_t i = (split > i_first ? split : i_first) + threadIdx.x;
-  uint32_t P = 0;
-  uint64_t m = 0;
-  uint2 c = make_uint2(0, 0);
-  if (i < np) {
-    P = __ldg(primes + i);
-    m = __ldg(magic + i);
-    c = __ldg(cinv + i);
-  }
-  // the loop is unrolled by two with the prefetched entries alternating
-  // between two register sets (fewer moves than rotating one set; measured)
-  auto one = [&](uint32_t Pq, uint64_t mq, uint2 cq) {
-    uint32_t k1 = len, k5 = len;
-    if ((uint64_t)Pq * Pq <= B && Pq < 0x80000000u) {
-      starts_from_inverse(K0, Pq, mq, cq, k1, k5);
-    } else {
-      uint64_t a1, a5;
-      if (tile_starts_within(B, Pq, mq, span6, a1, a5)) {
-        k1 = a1 < len ? (uint32_t)a1 : len;
-        k5 = a5 < len ? (uint32_t)a5 : len;
-      }
+  auto lane_loop = [&](auto &&one) {
+    uint32_t i = (split > i_first ? split : i_first) + threadIdx.x;
+    uint32_t P = 0;
+    uint64_t m = 0;
+    uint2 c = make_uint2(0, 0);
+    if (i < np) {
+      P = __ldg(primes + i);
+      m = __ldg(magic + i);
+      c = __ldg(cinv + i);
     }
-    // a plain loop per class: lane-band primes have few hits per tile, so
-    // the unrolled loop's set-up costs more than it saves (measured); k + P
-    // < 2^32
+    while (i < np) {
+      const uint32_t in = i + BLOCK;
+      uint32_t Pb = 0;
+      uint64_t mb = 0;
+      uint2 cb = make_uint2(0, 0);
+      if (in < np) {
+        Pb = __ldg(primes + in);
+        mb = __ldg(magic + in);
+        cb = __ldg(cinv + in);
+      }
+      one(P, m, c);
+      if (in >= np) break;
+      const uint32_t in2 = in + BLOCK;
+      if (in2 < np) {
+        P = __ldg(primes + in2);
+        m = __ldg(magic + in2);
+        c = __ldg(cinv + in2);
+      }
+      one(Pb, mb, cb);
+      i = in2;
+    }
+  };
+  // a plain loop per class: one-lane primes have few hits per tile, so the
+  // unrolled loop's set-up costs more than it saves (measured); k + P < 2^32
+  auto strike_from = [&](uint32_t Pq, uint32_t k1, uint32_t k5) {
     for (uint32_t k = k1; k < len; k += Pq) strike_one(s1, k, wmask, logW);
     for (uint32_t k = k5; k < len; k += Pq) strike_one(s5, k, wmask, logW);
   };
-  while (i < np) {
-    const uint32_t in = i + BLOCK;
-    uint32_t Pb = 0;
-    uint64_t mb = 0;
-    uint2 cb = make_uint2(0, 0);
-    if (in < np) {
-      Pb = __ldg(primes + in);
-      mb = __ldg(magic + in);
-      cb = __ldg(cinv + in);
-    }
-    one(P, m, c);
-    if (in >= np) break;
-    const uint32_t in2 = in + BLOCK;
-    if (in2 < np) {
-      P = __ldg(primes + in2);
-      m = __ldg(magic + in2);
-      c = __ldg(cinv + in2);
-    }
-    one(Pb, mb, cb);
-    i = in2;
+  if (all_sq) {  // every prime has P^2 <= B and P < 2^31: no clamp to test for
+    lane_loop([&](uint32_t Pq, uint64_t mq, uint2 cq) {
+      uint32_t k1, k5;
+      starts_from_inverse(K0, Pq, mq, cq, k1, k5);
+      strike_from(Pq, k1, k5);
+    });
+  } else {
+    lane_loop([&](uint32_t Pq, uint64_t mq, uint2 cq) {
+      uint32_t k1 = len, k5 = len;
+      if ((uint64_t)Pq * Pq <= B && Pq < 0x80000000u) {
+        starts_from_inverse(K0, Pq, mq, cq, k1, k5);
+      } else {
+        uint64_t a1, a5;
+        if (tile_starts_within(B, Pq, mq, span6, a1, a5)) {
+          k1 = a1 < len ? (uint32_t)a1 : len;
+          k5 = a5 < len ? (uint32_t)a5 : len;
+        }
+      }
+      strike_from(Pq, k1, k5);
+    });
   }
 }
 
