@@ -50,12 +50,18 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
   uint32_t *s5 = smem + W;
   uint2 *starts = (uint2 *)(smem + 2 * W);  // warp-band start indices
   __shared__ uint32_t sh_np, sh_next, sh_allsq;
+  __shared__ uint32_t sh_poff[kNumPatterns];  // pattern offsets of the tile about to be sieved
   __shared__ uint64_t sh_bin0;
   __shared__ int64_t sh_t1, sh_t5;
   __shared__ int sh_has_boundary;
   __shared__ uint64_t red[3 * NWARPS];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t np_prev = 0;  // warp 0: the previous tile's prime count
+  // the pattern offsets K0 mod period: computed once per tile by a few
+  // threads (for the next tile at the end of this one), not by every thread
+  if (threadIdx.x < (uint32_t)p.npat && blockIdx.x < p.ntiles)
+    sh_poff[threadIdx.x] = pattern_offset(p.k_begin + (uint64_t)blockIdx.x * p.L, p.pd[threadIdx.x]);
+  __syncthreads();
 
   for (uint32_t t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
     const uint64_t K0 = p.k_begin + (uint64_t)t * p.L;
@@ -98,7 +104,7 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
         }
       }
     }
-    presieve_copy<BLOCK>(s1, s5, tg, K0, p.sliced, p.pd, p.npat);
+    presieve_copy<BLOCK>(s1, s5, tg, K0, p.sliced, p.pd, p.npat, sh_poff);
     warp_band_starts<BLOCK>(starts, B, tg.len, p.primes, p.magic, p.cinv, p.i_first, p.i_split);
     __syncthreads();
 
@@ -169,6 +175,9 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
         }
       }
     }
+    const uint32_t tn = t + gridDim.x;  // the next tile's pattern offsets (a warp other than thread 0's)
+    if (threadIdx.x >= 32 && threadIdx.x < 32 + (uint32_t)p.npat && tn < p.ntiles)
+      sh_poff[threadIdx.x - 32] = pattern_offset(p.k_begin + (uint64_t)tn * p.L, p.pd[threadIdx.x - 32]);
     __syncthreads();
   }
 }

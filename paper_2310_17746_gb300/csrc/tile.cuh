@@ -61,18 +61,24 @@ struct TileGeom {
   uint32_t len;   // indices in use (<= 32 W)
 };
 
+// K0 mod period of pattern g (the tile's offset into it).
+__device__ __forceinline__ uint32_t pattern_offset(uint64_t K0, const PatternDesc &pd) {
+  return (uint32_t)(K0 - div_invariant(K0, pd.period, pd.magic) * pd.period);
+}
+
 // Presieve copy.  For pattern g (period P_g), the sliced pattern T_g holds, at
 // word j, bit b = pattern bit (j + b W) mod P_g; so tile word w is
 // T_g[(K0 mod P_g) + w], a contiguous, coalesced copy.  Words of all patterns
-// in use are ANDed.
+// in use are ANDed.  `o_given`, when given, holds the tile's offsets K0 mod
+// P_g (computed ahead by the caller); else every thread computes them.
 template <int BLOCK>
 __device__ __forceinline__ void presieve_copy(uint32_t *s1, uint32_t *s5, const TileGeom &tg, uint64_t K0,
                                               const uint32_t *__restrict__ sliced, const PatternDesc *pd,
-                                              int npat) {
+                                              int npat, const uint32_t *o_given = nullptr) {
   uint32_t o[kNumPatterns];
 #pragma unroll
   for (int g = 0; g < kNumPatterns; g++)
-    if (g < npat) o[g] = (uint32_t)(K0 - div_invariant(K0, pd[g].period, pd[g].magic) * pd[g].period);
+    if (g < npat) o[g] = o_given ? o_given[g] : pattern_offset(K0, pd[g]);
   for (uint32_t w = threadIdx.x; w < tg.W; w += BLOCK) {
     uint32_t v1 = 0xFFFFFFFFu, v5 = 0xFFFFFFFFu;
 #pragma unroll
