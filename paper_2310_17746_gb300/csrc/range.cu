@@ -109,11 +109,14 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
     __syncthreads();
 
     strike_primes<BLOCK>(s1, s5, B, tg, p.primes, p.magic, p.cinv, starts, p.i_first, p.i_split, sh_np,
-                         sh_allsq != 0, &sh_next);
+                         sh_allsq != 0, &sh_next, K0);
     __syncthreads();
 
-    const ValidRange v = valid_range(p.lo, p.hi, B, tg.len);
-    fixup_tile<BLOCK>(s1, s5, tg, K0, v, p.npat);  // ends with a barrier when it changes the tile
+    // a full tile above the presieved primes and inside [lo, hi) needs no
+    // fix-up (valid_range would give [0, 32 W) in both classes)
+    const bool interior = 6 * K0 > 131 && p.lo <= B + 1 && p.hi >= B + 6ull * 32 * W && tg.len == 32 * W;
+    if (!interior)  // ends with a barrier when it changes the tile
+      fixup_tile<BLOCK>(s1, s5, tg, K0, valid_range(p.lo, p.hi, B, tg.len), p.npat);
 
     // popcount, checksum, and the count below the segment boundary (if any).
     // Word w holds indices w + b W: their values sum to
@@ -151,9 +154,20 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
       planes.add1(b);
     }
     const uint32_t bs = planes.index_sum();
-    uint64_t cnt = (uint64_t)c1 + c5, below = below32;
-    uint64_t sum = (uint64_t)c1 * (6 * K0 + 1) + (uint64_t)c5 * (6 * K0 + 5) + 6ull * sw + 6ull * W * bs;
-    block_sum3<BLOCK>(cnt, sum, below, red);
+    // the sums over the warp in 32 bits (a warp's c1, c5 < 2^17, sw < 2^31,
+    // bs < 2^23: they fit), then the 64-bit count and checksum once per warp
+    uint32_t wc1 = c1, wc5 = c5, wsw = sw, wbs = bs, wbl = below32;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      wc1 += __shfl_down_sync(kFullMask, wc1, o);
+      wc5 += __shfl_down_sync(kFullMask, wc5, o);
+      wsw += __shfl_down_sync(kFullMask, wsw, o);
+      wbs += __shfl_down_sync(kFullMask, wbs, o);
+      wbl += __shfl_down_sync(kFullMask, wbl, o);
+    }
+    uint64_t cnt = (uint64_t)wc1 + wc5, below = wbl;
+    uint64_t sum = (uint64_t)wc1 * (6 * K0 + 1) + (uint64_t)wc5 * (6 * K0 + 5) + 6ull * wsw + 6ull * W * wbs;
+    block_sum3_warps<BLOCK>(cnt, sum, below, red);
     if (threadIdx.x == 0) {
       if (K0 == 0) {  // 2 and 3 are outside the residue arrays (Section 2.1)
         const uint64_t e2 = (p.lo <= 2 && 2 < p.hi), e3 = (p.lo <= 3 && 3 < p.hi);

@@ -161,7 +161,7 @@ __device__ __forceinline__ void warp_band_starts(uint2 *starts, uint64_t B, uint
 // one at a time through a shared counter so that warps finish together; the
 // rest by one lane each, which locates the prime's first hits from its
 // inverse-of-6 constants (cinv; the Table 1 start, see starts_from_inverse)
-// or, where the P^2 clamp can apply, with Table 1 itself (all_sq: the caller
+// or, where the P^2 clamp can apply, with Table 1 itself (K0 = B / 6; all_sq: the caller
 // knows that every prime below np has P^2 <= B and P < 2^31, so the test per
 // prime is skipped).  (Loading the
 // constants only for primes below the tile span, so that larger ones keep a
@@ -171,7 +171,7 @@ __device__ __forceinline__ void strike_primes(uint32_t *s1, uint32_t *s5, uint64
                                               const uint32_t *__restrict__ primes,
                                               const uint64_t *__restrict__ magic, const uint2 *__restrict__ cinv,
                                               const uint2 *starts, uint32_t i_first, uint32_t i_split, uint32_t np,
-                                              bool all_sq, uint32_t *next) {
+                                              bool all_sq, uint32_t *next, uint64_t K0) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t split = i_split < np ? i_split : np;
   const uint32_t len = tg.len, wmask = tg.W - 1, logW = tg.logW, span6 = 6 * tg.len;
@@ -190,7 +190,6 @@ __device__ __forceinline__ void strike_primes(uint32_t *s1, uint32_t *s5, uint64
   // current prime is struck so that their latency overlaps the strikes.  The
   // loop is unrolled by two with the prefetched entries alternating between
   // two register sets (fewer moves than rotating one set; measured).
-  const uint64_t K0 = B / 6;
   auto lane_loop = [&](auto &&one) {
     uint32_t i = (split > i_first ? split : i_first) + threadIdx.x;
     uint32_t P = 0;
@@ -376,6 +375,31 @@ struct BitPlanes {
     return s;
   }
 };
+
+// As block_sum3, for values that lane 0 of each warp already holds summed
+// over its warp: only the sum over the warps remains (result in thread 0).
+template <int BLOCK>
+__device__ __forceinline__ void block_sum3_warps(uint64_t &a, uint64_t &b, uint64_t &c, uint64_t *red) {
+  constexpr int NWARPS = BLOCK / 32;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[warp] = a;
+    red[NWARPS + warp] = b;
+    red[2 * NWARPS + warp] = c;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    a = lane < NWARPS ? red[lane] : 0;
+    b = lane < NWARPS ? red[NWARPS + lane] : 0;
+    c = lane < NWARPS ? red[2 * NWARPS + lane] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(kFullMask, a, o);
+      b += __shfl_down_sync(kFullMask, b, o);
+      c += __shfl_down_sync(kFullMask, c, o);
+    }
+  }
+}
 
 template <int BLOCK>
 __device__ __forceinline__ void block_sum3(uint64_t &a, uint64_t &b, uint64_t &c, uint64_t *red) {
