@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK > 0 ? 1024 / BLOCK : 1)) 
     const bool merged = (qd.flags & kQueryMerged) != 0;
 
     if (it.t == kStrip) {
-      // large primes over the whole query: one Table 1 evaluation per prime
+      // large primes over the whole query: one start computation per prime
       // for the query base, then every hit up to the query's end
       const uint64_t Bq = 6 * qd.k_begin;
       const uint64_t span = qd.k_end - qd.k_begin;

@@ -12,7 +12,7 @@
 //     sized to the query (a power of two >= 1024 indices per class, at most
 //     the batch tile size), so narrow queries use small tiles.
 //   * strip item: base primes [i0, i1) that exceed the tile length, applied to
-//     a whole query at once: each prime's first index comes from one Table 1
+//     a whole query at once: each prime's first index comes from one start
 //     evaluation for the query, then every later hit (index + P) is cleared
 //     with an atomic AND in the query's bitmap in global memory.  This is the
 //     work a bucket sieve saves for primes larger than a segment: a prime is

@@ -3,8 +3,9 @@
 //
 // Kernel structure (Section 4, Figure 4, mapped to a GPU): the range is cut
 // into tiles of L indices per residue class; CTAs take tiles in grid-stride
-// order.  Per tile: wheel presieve copy -> Table 1 start indices and strikes
-// for every base prime 23 <= P <= isqrt(tile end) -> fix-ups -> popcount,
+// order.  Per tile: presieve copy -> start indices (Table 1, or the equal
+// inverse-of-6 form) and strikes for every base prime above the presieved
+// ones up to isqrt(tile end) -> fix-ups -> popcount,
 // checksum and per-segment counts (count mode) or bitmap write-out (list mode,
 // followed by a scan of per-tile counts and a compaction kernel).
 #include <algorithm>
