@@ -157,6 +157,19 @@ int sieve_primes_u32(sieve_ctx *ctx, uint64_t n, uint32_t *out, size_t cap, size
 int sieve_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, int mode, sieve_count_result *cnt,
                 uint64_t *out, size_t cap, size_t *n_out, unsigned flags);
 
+/* The plain GPU sieve of [lo, hi), the comparison point for the segmented
+ * path (Section 1.1 / Figure 1 done directly, one range per call): one bit per
+ * odd number of the range in a bitmap in global memory, every odd multiple
+ * m >= max(p^2, lo) of every odd base prime p cleared with a global atomic
+ * AND (a prime's multiples spread over as many CTAs as they need), then a
+ * popcount pass, or a count / scan / write pass for the list.  No residue
+ * classes, presieve, shared-memory segments or Table 1.  Same arguments,
+ * outputs and errors as sieve_range (the list is uint64), plus OOM when the
+ * bitmap (one byte per 16 numbers, e.g. 62.5 GB for [2, 1e12]) does not fit
+ * on the device; it allocates and frees the bitmap in every call. */
+int sieve_range_naive(sieve_ctx *ctx, uint64_t lo, uint64_t hi, int mode, sieve_count_result *cnt,
+                      uint64_t *out, size_t cap, size_t *n_out, unsigned flags);
+
 /* Count, checksum and per-segment counts of the primes in [lo, hi).
  * Segment s is the value interval [s*seg_width, (s+1)*seg_width); counts[i]
  * holds segment floor(lo / seg_width) + i, so ncounts must equal
@@ -231,13 +244,32 @@ int sieve_range_each(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, con
  *   sieve_autotune_batch: batch_tile_bits x block_threads x chunk_primes on
  *     the given batch (host arrays, as sieve_range_batch); allocates and frees
  *     its own device outputs.
- *   sieve_autotune_range: tile_bits x block_threads x group_hits x
- *     presieve_groups on the count of [lo, hi) (a sample of the ranges to
- *     come; every candidate sieves it reps + 1 times). */
+ *   sieve_autotune_range: tile_bits {2^18, 2^19} x block_threads {512, 1024}
+ *     x ctas_per_sm {0, 1, 2} (512 threads only) x group_hits {3, 4, 5, 6, 8}
+ *     x presieve_groups {5, 6, 7, 8} on the count of [lo, hi) (a sample of the
+ *     ranges to come; every candidate sieves it reps + 1 times). */
 int sieve_autotune_batch(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, const uint8_t *mode, size_t nq,
                          int reps, sieve_options *best, double *best_ms);
 int sieve_autotune_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, int reps, sieve_options *best,
                          double *best_ms);
+
+/* A cache of tuned options in a small JSON file, keyed by (device name, SM
+ * count, workload name), so that a tuning run is paid once per device and
+ * workload class.  The file holds {"sieve_tune_cache": 1, "entries": [...]}
+ * with one entry per line; the workload name is any caller-chosen label of at
+ * most 200 characters without quotes, backslashes or control characters.
+ *   sieve_tune_cache_store: writes the context's current options (with `ms`,
+ *     the tuned time, for information) under this device and workload,
+ *     replacing an entry with the same key and keeping the others; the file
+ *     is written to path + ".tmp" and renamed over path.
+ *   sieve_tune_cache_load: if the file has an entry for this device and
+ *     workload, validates it and makes it the context's options (*found = 1,
+ *     *ms = its time; ms may be NULL); else leaves the options unchanged with
+ *     *found = 0 (a missing file is not an error).
+ * Errors: INVALID (NULL argument, bad name, unwritable file, invalid entry),
+ * CUDA. */
+int sieve_tune_cache_store(sieve_ctx *ctx, const char *path, const char *workload, double ms);
+int sieve_tune_cache_load(sieve_ctx *ctx, const char *path, const char *workload, int *found, double *ms);
 
 /* ------------------------------------------------------------- serving */
 
@@ -314,21 +346,23 @@ void sieve_server_stop(sieve_server *srv);
  * caller's DEVICE buffer out[0..cap), *n_out = their number, *cnt (host, may
  * be NULL) = count and checksum.  It allocates nothing: no cudaMalloc,
  * cudaFree or allocating library routine.  It uses the context's base table
- * and accumulators (made by sieve_create) and, as scratch for per-tile
- * bitmaps, counts and offsets, one file-scope device array of
- * SIEVE_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
- * exit.  The bitmaps take about one bit per 3 numbers, so a call covers a
- * range of at most about 3.8e8 numbers; wider ranges return
- * SIEVE_ERR_INVALID with a message giving the limit.  It does not presieve
- * (the presieve patterns are allocated on demand by the other calls), so it
- * is slower than sieve_range.
+ * and accumulators and, as scratch for per-tile bitmaps, counts and offsets,
+ * one file-scope device array of SIEVE_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading the library holds until exit.  The array's device address is looked
+ * up (cudaGetSymbolAddress, with the context's device current) by sieve_create,
+ * which is also when the array is made under lazy module loading; the entry
+ * point itself does no set-up.  The bitmaps take one bit per candidate, about
+ * one byte per 24 numbers: with the default tile length (2^19 candidates per
+ * class) a call covers any range of at most 399,507,452 numbers; a wider
+ * range returns SIEVE_ERR_INVALID with a message giving the limit for the
+ * context's tile length.  It does not presieve (the presieve patterns are
+ * allocated on demand by the other calls), so it is slower than sieve_range.
  *
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  All calls share the one array: calls that
- * overlap on the GPU (on different streams or from different threads) race
- * and give wrong results.  Errors: INVALID, RANGE, CAPACITY (nothing written
- * when the list does not fit), CUDA. */
+ * All calls share the one array and it keeps the previous call's contents
+ * (each call writes every entry it reads).  Calls that overlap on the GPU (on
+ * different streams, contexts or threads) race and give wrong results.
+ * Errors: INVALID, RANGE, CAPACITY (nothing written when the list does not
+ * fit), CUDA. */
 int sieve_range_list_noalloc(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *out, size_t cap,
                              size_t *n_out, sieve_count_result *cnt);
 

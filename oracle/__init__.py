@@ -32,11 +32,11 @@ class OracleError(RuntimeError):
 
 
 class BaseTable:
-    """Primes <= limit (Figure 1), built once and reused across many range calls."""
+    """Primes <= limit (Section 1.1), built once and reused across many range calls."""
 
     def __init__(self, limit: int, oracle: "Oracle | None" = None):
         self.limit = int(limit)
-        self.primes = (oracle or default()).fig1_primes(self.limit)
+        self.primes = (oracle or default()).primes_upto(self.limit)
 
 
 class Oracle:
@@ -46,8 +46,8 @@ class Oracle:
         lib = ctypes.CDLL(libpath)
         lib.oracle_isqrt.argtypes = [_u64]
         lib.oracle_isqrt.restype = _u64
-        lib.oracle_fig1_primes.argtypes = [_u64, _p, ctypes.c_size_t]
-        lib.oracle_fig1_primes.restype = ctypes.c_int64
+        lib.oracle_primes_upto.argtypes = [_u64, _p, ctypes.c_size_t]
+        lib.oracle_primes_upto.restype = ctypes.c_int64
         lib.oracle_range.argtypes = [_u64, _u64, _p, ctypes.c_size_t, _u64, ctypes.c_int,
                                      _p, _p, _p, ctypes.c_size_t, _p, _u64, _p, ctypes.c_size_t]
         lib.oracle_range.restype = ctypes.c_int
@@ -79,13 +79,15 @@ class Oracle:
     def default_threads(self) -> int:
         return int(self.lib.oracle_default_threads())
 
-    def fig1_primes(self, n: int) -> np.ndarray:
-        """All primes <= n as uint32 (Figure 1)."""
-        k = self.lib.oracle_fig1_primes(n, None, 0)
+    def primes_upto(self, n: int) -> np.ndarray:
+        """All primes <= n as uint32 (Section 1.1)."""
+        k = self.lib.oracle_primes_upto(n, None, 0)
         if k < 0:
-            raise OracleError(f"fig1_primes({n}) failed with status {k}")
+            raise OracleError(f"primes_upto({n}) failed with status {k}")
         out = np.empty(max(k, 1), dtype=np.uint32)
-        self.lib.oracle_fig1_primes(n, out.ctypes.data, k)
+        k2 = self.lib.oracle_primes_upto(n, out.ctypes.data, k)
+        if k2 != k:
+            raise OracleError(f"primes_upto({n}) failed with status {k2}")
         return out[:k]
 
     def count_range(self, lo: int, hi: int, base: BaseTable | None = None, threads: int = 0):
@@ -161,8 +163,8 @@ def default_threads():
     return default().default_threads()
 
 
-def fig1_primes(n):
-    return default().fig1_primes(n)
+def primes_upto(n):
+    return default().primes_upto(n)
 
 
 def count_range(lo, hi, base=None, threads=0):
@@ -195,6 +197,6 @@ def raw_range(*args):
 
 __all__ = [
     "Oracle", "BaseTable", "base_table", "default", "count_range", "list_range",
-    "segment_counts", "nbins", "fig1_primes", "isqrt", "is_prime_td", "is_prime_mr",
+    "segment_counts", "nbins", "primes_upto", "isqrt", "is_prime_td", "is_prime_mr",
     "first_class_multiple", "default_threads", "OracleError", "raw_range",
 ]

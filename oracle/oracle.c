@@ -36,30 +36,38 @@ uint64_t oracle_isqrt(uint64_t n) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Figure 1, written out: A[2..n] = true, strike i*i, i*i + i, ... for every
- * i with i*i <= n that is still true. */
-int64_t oracle_fig1_primes(uint64_t n, uint32_t *out, size_t cap) {
+/* The primes <= n (Section 1.1: all primes from 2 through n), by the
+ * definition of primality: m >= 2 is prime iff no prime q <= isqrt(m) divides
+ * m.  A composite m <= n has its smallest prime factor q <= isqrt(m) <= isqrt(n)
+ * and m >= q*q, so the primes <= n are what survives in [2, n] once every
+ * multiple >= q*q of every prime q <= isqrt(n) is crossed off -- which is what
+ * oracle_range does for [0, n + 1) given those primes.  They come from this
+ * same function for isqrt(n); the chain ends at n < 4, where isqrt(n) < 2 and
+ * nothing needs crossing off. */
+int64_t oracle_primes_upto(uint64_t n, uint32_t *out, size_t cap) {
   if (n < 2) return 0;
   if (n > 0xFFFFFFFFull) return ORACLE_ERR_RANGE; /* primes are stored as uint32 */
-  uint8_t *A = (uint8_t *)malloc((size_t)n + 1);
-  if (!A) return ORACLE_ERR_OOM;
-  A[0] = 0;
-  A[1] = 0;
-  memset(A + 2, 1, (size_t)n - 1);
-  for (uint64_t i = 2; i * i <= n; i++) {
-    if (A[i]) {
-      for (uint64_t j = i * i; j <= n; j += i) A[j] = 0;
+  const uint64_t r = oracle_isqrt(n);
+  int64_t nb = oracle_primes_upto(r, NULL, 0);
+  if (nb < 0) return nb;
+  uint32_t *base = (uint32_t *)malloc(((size_t)nb + 1) * sizeof(uint32_t));
+  if (!base) return ORACLE_ERR_OOM;
+  oracle_primes_upto(r, base, (size_t)nb);
+  uint64_t count = 0;
+  int rc = oracle_range(0, n + 1, base, (size_t)nb, r, 0, &count, NULL, NULL, 0, NULL, 0, NULL, 0);
+  if (rc == ORACLE_OK && out && cap) {
+    uint64_t *tmp = (uint64_t *)malloc(((size_t)count + 1) * sizeof(uint64_t));
+    size_t got = 0;
+    if (!tmp) {
+      rc = ORACLE_ERR_OOM;
+    } else {
+      rc = oracle_range(0, n + 1, base, (size_t)nb, r, 0, NULL, NULL, tmp, (size_t)count, &got, 0, NULL, 0);
+      for (size_t i = 0; rc == ORACLE_OK && i < got && i < cap; i++) out[i] = (uint32_t)tmp[i];
+      free(tmp);
     }
   }
-  int64_t k = 0;
-  for (uint64_t i = 2; i <= n; i++) {
-    if (A[i]) {
-      if (out && (size_t)k < cap) out[k] = (uint32_t)i;
-      k++;
-    }
-  }
-  free(A);
-  return k;
+  free(base);
+  return rc == ORACLE_OK ? (int64_t)count : rc;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -171,11 +179,11 @@ int oracle_range(uint64_t lo, uint64_t hi, const uint32_t *base, size_t nbase,
   uint64_t s = oracle_isqrt(hi - 1);
   uint32_t *own = NULL;
   if (base == NULL) {
-    int64_t np = oracle_fig1_primes(s, NULL, 0);
+    int64_t np = oracle_primes_upto(s, NULL, 0);
     if (np < 0) return (int)np;
     own = (uint32_t *)malloc(((size_t)np + 1) * sizeof(uint32_t));
     if (!own) return ORACLE_ERR_OOM;
-    oracle_fig1_primes(s, own, (size_t)np);
+    oracle_primes_upto(s, own, (size_t)np);
     base = own;
     nbase = (size_t)np;
   } else if (base_limit < s) {

@@ -39,14 +39,17 @@ extern "C" {
  * then a final +-1 correction).  Valid for every n < 2^64. */
 uint64_t oracle_isqrt(uint64_t n);
 
-/* Figure 1 verbatim: A[2..n] = true; for i = 2.. while i*i <= n, if A[i],
- * clear i*i, i*i+i, ... n.  Writes the primes <= n (increasing) to out[0..cap)
- * and returns how many primes <= n there are (which may exceed cap). */
-int64_t oracle_fig1_primes(uint64_t n, uint32_t *out, size_t cap);
+/* The primes <= n (n < 2^32; Section 1.1), from the definition: m >= 2 is
+ * prime iff no prime q <= isqrt(m) divides it.  The primes q <= isqrt(n) come
+ * from this function itself (recursively, down to n < 4), and oracle_range
+ * crosses off their multiples >= q*q in [0, n].  Writes the primes <= n
+ * (increasing) to out[0..cap) and returns how many primes <= n there are
+ * (which may exceed cap), or a negative status. */
+int64_t oracle_primes_upto(uint64_t n, uint32_t *out, size_t cap);
 
 /* Primes in [lo, hi) by the segmented byte sieve described above.
  *   base / nbase / base_limit : every prime <= base_limit, increasing (from
- *                    oracle_fig1_primes(base_limit)), or base == NULL to let
+ *                    oracle_primes_upto(base_limit)), or base == NULL to let
  *                    the call build them itself.  base_limit < isqrt(hi - 1)
  *                    is ORACLE_ERR_RANGE.
  *   nthreads       : host threads; <= 0 means every core this process may use.

@@ -121,6 +121,10 @@ SIGNATURES = {
     "sieve_set_phase_timing": (_i, [_p, _i]),
     "sieve_get_phase_times": (_i, [_p, _p]),
     "sieve_next": (_i, [_p, _u64, _sz, _p, ctypes.POINTER(_sz), _u]),
+    "sieve_range_naive": (_i, [_p, _u64, _u64, _i, _p, _p, _sz, ctypes.POINTER(_sz), _u]),
+    "sieve_tune_cache_store": (_i, [_p, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_double]),
+    "sieve_tune_cache_load": (_i, [_p, ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(_i),
+                                   ctypes.POINTER(ctypes.c_double)]),
 }
 
 
@@ -177,19 +181,38 @@ def _is_torch_cuda(x) -> bool:
     return hasattr(x, "is_cuda") and bool(x.is_cuda)
 
 
-def _ptr_and_flag(x):
-    """(pointer, flags) for an output buffer: torch CUDA tensor or numpy array."""
+_TORCH_INT_DTYPES = {"torch.int64": 8, "torch.uint64": 8, "torch.int32": 4, "torch.uint32": 4}
+
+
+def _ptr_and_flag(x, esizes=(8,), min_numel: int = 0, what: str = "buffer"):
+    """(pointer, flags, capacity in elements) for an output buffer: a torch
+    CUDA tensor or a numpy array of integers whose element size is one of
+    `esizes` bytes, contiguous, with at least `min_numel` elements.  Anything
+    else raises before the library is called, so that a kernel never writes
+    past a buffer that is smaller than its element count suggests."""
     if x is None:
-        return None, 0
+        return None, 0, 0
     if _is_torch_cuda(x):
+        esize = _TORCH_INT_DTYPES.get(str(x.dtype))
+        if esize is None or esize not in esizes or x.element_size() != esize:
+            raise TypeError(f"{what}: device buffer must be an integer tensor of {' or '.join(map(str, esizes))}"
+                            f"-byte elements, got {x.dtype}")
         if not x.is_contiguous():
-            raise ValueError("device buffers must be contiguous")
-        return x.data_ptr(), OUT_DEVICE
+            raise ValueError(f"{what}: device buffers must be contiguous")
+        n = int(x.numel())
+        if n < min_numel:
+            raise ValueError(f"{what}: device buffer needs at least {min_numel} elements, has {n}")
+        return x.data_ptr(), OUT_DEVICE, n
     if isinstance(x, np.ndarray):
-        if not x.flags.c_contiguous:
-            raise ValueError("host buffers must be C-contiguous")
-        return x.ctypes.data, 0
-    raise TypeError("expected a numpy array or a torch CUDA tensor")
+        if x.dtype.kind not in "iu" or x.dtype.itemsize not in esizes:
+            raise TypeError(f"{what}: host buffer must be an integer array of "
+                            f"{' or '.join(map(str, esizes))}-byte elements, got {x.dtype}")
+        if not x.flags.c_contiguous or not x.flags.writeable:
+            raise ValueError(f"{what}: host buffers must be C-contiguous and writeable")
+        if x.size < min_numel:
+            raise ValueError(f"{what}: host buffer needs at least {min_numel} elements, has {x.size}")
+        return x.ctypes.data, 0, int(x.size)
+    raise TypeError(f"{what}: expected a numpy array or a torch CUDA tensor")
 
 
 def _current_stream_handle(device: int):
@@ -296,11 +319,10 @@ class Sieve:
             out = np.empty(max(c, 1), dtype=dtype)
             got = self.primes(n, out)
             return out[:got]
-        ptr, flags = _ptr_and_flag(out)
+        ptr, flags, cap = _ptr_and_flag(out, (4, 8), what="out")
         nout = _sz(0)
         esize = out.element_size() if _is_torch_cuda(out) else out.itemsize
         fn = self._lib.sieve_primes_u32 if esize == 4 else self._lib.sieve_primes
-        cap = out.numel() if _is_torch_cuda(out) else out.size
         _check(fn(self._h, int(n), ptr, cap, ctypes.byref(nout), flags), "sieve_primes")
         return int(nout.value)
 
@@ -309,7 +331,9 @@ class Sieve:
         int64 tensor of 2 elements the result is written there (and the call
         is only enqueued when asynchronous=True)."""
         if out is not None:
-            ptr, flags = _ptr_and_flag(out)
+            if not _is_torch_cuda(out):
+                raise TypeError("out: expected a torch CUDA int64 tensor of 2 elements")
+            ptr, flags, _ = _ptr_and_flag(out, (8,), 2, what="out")
             if asynchronous:
                 flags |= ASYNC
             _check(self._lib.sieve_range(self._h, int(lo), int(hi), COUNT, ptr, None, 0, None, flags),
@@ -327,11 +351,32 @@ class Sieve:
             out = np.empty(max(c, 1), dtype=np.uint64)
             got = self.range_list(lo, hi, out)
             return out[:got]
-        ptr, flags = _ptr_and_flag(out)
-        cap = out.numel() if _is_torch_cuda(out) else out.size
+        ptr, flags, cap = _ptr_and_flag(out, (8,), what="out")
         nout = _sz(0)
         _check(self._lib.sieve_range(self._h, int(lo), int(hi), LIST, None, ptr, cap, ctypes.byref(nout), flags),
                "sieve_range")
+        return int(nout.value)
+
+    def naive_count(self, lo: int, hi: int) -> CountAndSum:
+        """(count, checksum) of [lo, hi) by the plain global-bitmap GPU sieve
+        (sieve_range_naive), the comparison point for the segmented path."""
+        r = CountResult()
+        _check(self._lib.sieve_range_naive(self._h, int(lo), int(hi), COUNT, ctypes.cast(ctypes.byref(r), _p),
+                                           None, 0, None, 0), "sieve_range_naive")
+        return CountAndSum(r.count, r.checksum)
+
+    def naive_list(self, lo: int, hi: int, out=None):
+        """Primes in [lo, hi) as uint64 by the plain GPU sieve: into `out`
+        (numpy uint64 or torch CUDA int64; returns the count) or a new array."""
+        if out is None:
+            c = self.naive_count(lo, hi).count
+            out = np.empty(max(c, 1), dtype=np.uint64)
+            got = self.naive_list(lo, hi, out)
+            return out[:got]
+        ptr, flags, cap = _ptr_and_flag(out, (8,), what="out")
+        nout = _sz(0)
+        _check(self._lib.sieve_range_naive(self._h, int(lo), int(hi), LIST, None, ptr, cap, ctypes.byref(nout),
+                                           flags), "sieve_range_naive")
         return int(nout.value)
 
     def next_primes(self, after: int, k: int, out=None):
@@ -342,8 +387,7 @@ class Sieve:
             out = np.empty(max(int(k), 1), dtype=np.uint64)
             n = self.next_primes(after, k, out)
             return out[:n]
-        ptr, flags = _ptr_and_flag(out)
-        cap = out.numel() if _is_torch_cuda(out) else out.size
+        ptr, flags, cap = _ptr_and_flag(out, (8,), what="out")
         if k > cap:
             raise ValueError("out holds fewer than k elements")
         nout = _sz(0)
@@ -355,9 +399,10 @@ class Sieve:
         entry point that allocates nothing; returns (number, count/checksum)."""
         if not _is_torch_cuda(out):
             raise TypeError("out must be a torch CUDA tensor")
+        ptr, _, cap = _ptr_and_flag(out, (8,), what="out")
         nout = _sz(0)
         r = CountResult()
-        _check(self._lib.sieve_range_list_noalloc(self._h, int(lo), int(hi), out.data_ptr(), out.numel(),
+        _check(self._lib.sieve_range_list_noalloc(self._h, int(lo), int(hi), ptr, cap,
                                                   ctypes.byref(nout), ctypes.cast(ctypes.byref(r), _p)),
                "sieve_range_list_noalloc")
         return int(nout.value), CountAndSum(r.count, r.checksum)
@@ -374,12 +419,12 @@ class Sieve:
             if not (_is_torch_cuda(cnt) and _is_torch_cuda(offsets) and (values is None or _is_torch_cuda(values))):
                 raise TypeError("device mode needs cnt, offsets (and values) as torch CUDA tensors")
             flags = OUT_DEVICE
-        vptr = None if values is None else _ptr_and_flag(values)[0]
-        cap = 0 if values is None else (values.numel() if _is_torch_cuda(values) else values.size)
+        vptr, _, cap = _ptr_and_flag(values, (8,), what="values")
+        cptr = _ptr_and_flag(cnt, (8,), 2 * nq, what="cnt")[0]
+        optr = _ptr_and_flag(offsets, (8,), nq + 1, what="offsets")[0]
         nout = _sz(0)
         rc = getattr(self._lib, fname)(self._h, lo.ctypes.data, hi.ctypes.data, mode.ctypes.data, nq,
-                                       _ptr_and_flag(cnt)[0], _ptr_and_flag(offsets)[0], vptr, cap,
-                                       ctypes.byref(nout), flags)
+                                       cptr, optr, vptr, cap, ctypes.byref(nout), flags)
         return rc, int(nout.value)
 
     def range_batch(self, lo, hi, mode, cnt=None, offsets=None, values=None, naive: bool = False):
@@ -432,6 +477,21 @@ class Sieve:
                                               ctypes.byref(ms)), "sieve_autotune_range")
         return o.as_dict(), float(ms.value)
 
+    def tune_cache_store(self, path: str, workload: str, ms: float = 0.0) -> None:
+        """Save the context's current options in the JSON tuning cache at
+        `path` under (this device, its SM count, `workload`)."""
+        _check(self._lib.sieve_tune_cache_store(self._h, str(path).encode(), workload.encode(), float(ms)),
+               "sieve_tune_cache_store")
+
+    def tune_cache_load(self, path: str, workload: str):
+        """Options from the tuning cache for (this device, `workload`): made
+        the context's and returned as (options, ms); None if absent."""
+        found = _i(0)
+        ms = ctypes.c_double(0.0)
+        _check(self._lib.sieve_tune_cache_load(self._h, str(path).encode(), workload.encode(), ctypes.byref(found),
+                                               ctypes.byref(ms)), "sieve_tune_cache_load")
+        return (self.options(), float(ms.value)) if found.value else None
+
     @staticmethod
     def nbins(lo: int, hi: int, seg_width: int) -> int:
         return 0 if hi <= lo else (hi - 1) // seg_width - lo // seg_width + 1
@@ -443,8 +503,10 @@ class Sieve:
         torch CUDA int64 tensors): fills them and returns None."""
         nb = self.nbins(lo, hi, seg_width)
         if counts is not None and _is_torch_cuda(counts):
-            cptr, flags = _ptr_and_flag(counts)
-            tptr = total.data_ptr() if total is not None else None
+            cptr, flags, _ = _ptr_and_flag(counts, (8,), nb, what="counts")
+            if total is not None and not _is_torch_cuda(total):
+                raise TypeError("total: expected a torch CUDA int64 tensor of 2 elements")
+            tptr = _ptr_and_flag(total, (8,), 2, what="total")[0]
             if asynchronous:
                 flags |= ASYNC
             _check(self._lib.sieve_segment_counts(self._h, int(lo), int(hi), int(seg_width), cptr, nb, tptr, flags),
@@ -452,8 +514,9 @@ class Sieve:
             return None
         if counts is None:
             counts = np.zeros(max(nb, 1), dtype=np.uint64)
+        cptr = _ptr_and_flag(counts, (8,), nb, what="counts")[0]
         r = CountResult()
-        _check(self._lib.sieve_segment_counts(self._h, int(lo), int(hi), int(seg_width), counts.ctypes.data, nb,
+        _check(self._lib.sieve_segment_counts(self._h, int(lo), int(hi), int(seg_width), cptr, nb,
                                               ctypes.cast(ctypes.byref(r), _p), 0), "sieve_segment_counts")
         return CountAndSum(r.count, r.checksum), counts[:nb]
 
@@ -495,8 +558,7 @@ class Server:
         r = CountResult()
         n = _sz(0)
         if out is not None:
-            ptr, flags = _ptr_and_flag(out)
-            cap = out.numel() if _is_torch_cuda(out) else out.size
+            ptr, flags, cap = _ptr_and_flag(out, (8,), what="out")
             rc = self._lib.sieve_server_poll(self._h, int(rid), ctypes.cast(ctypes.byref(r), _p), ptr, cap,
                                              ctypes.byref(n), flags)
             if rc == PENDING:

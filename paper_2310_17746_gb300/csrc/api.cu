@@ -464,6 +464,8 @@ extern "C" int sieve_create(sieve_ctx **ctx, uint64_t max_hi, int device, void *
       rc = cuda_fail(e, "context allocation");
       break;
     }
+    // the no-allocation entry point's scratch address, with the device current
+    if ((rc = noalloc_setup(c)) != SIEVE_OK) break;
     const uint64_t limit = std::max<uint64_t>(isqrt_u64(max_hi - 1), 1u << 16);
     rc = build_base_table(c, limit);
   } while (0);

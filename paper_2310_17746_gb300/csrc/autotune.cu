@@ -9,7 +9,9 @@
 // compared with the first candidate's, so a tunable can never change an
 // answer silently.
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "sieve_internal.cuh"
@@ -149,22 +151,29 @@ extern "C" int sieve_autotune_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, in
       rc = cuda_fail(e, "autotune allocation");
       break;
     }
-    const uint32_t tiles[] = {1u << 17, 1u << 18, 1u << 19};
+    // tile length (Section 5's array size), threads per CTA, CTAs per SM, the
+    // warp/lane split and the presieve depth
+    const uint32_t tiles[] = {1u << 18, 1u << 19};
     const uint32_t threads[] = {512, 1024};
-    const uint32_t ghs[] = {2, 4, 8};
-    const uint32_t groups[] = {1, 2, 3, 4};
+    const uint32_t ctas[] = {0, 1, 2};
+    const uint32_t ghs[] = {3, 4, 5, 6, 8};
+    const uint32_t groups[] = {5, 6, 7, 8};
     std::vector<sieve_options> cand;
     for (uint32_t tb : tiles)
       for (uint32_t th : threads)
-        for (uint32_t gh : ghs)
-          for (uint32_t g : groups) {
-            sieve_options o = orig;
-            o.tile_bits = tb;
-            o.block_threads = th;
-            o.group_hits = gh;
-            o.presieve_groups = g;
-            cand.push_back(o);
-          }
+        for (uint32_t cs : ctas) {
+          if (cs && th == 1024) continue;  // a 1024-thread CTA fits once per SM anyway
+          for (uint32_t gh : ghs)
+            for (uint32_t g : groups) {
+              sieve_options o = orig;
+              o.tile_bits = tb;
+              o.block_threads = th;
+              o.ctas_per_sm = cs;
+              o.group_hits = gh;
+              o.presieve_groups = g;
+              cand.push_back(o);
+            }
+        }
     bool have_ref = false;
     for (const sieve_options &o : cand) {
       const uint32_t tb = o.tile_bits, th = o.block_threads, gh = o.group_hits, g = o.presieve_groups;
@@ -191,9 +200,9 @@ extern "C" int sieve_autotune_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, in
         ref = got;
         have_ref = true;
       } else if (ref.count != got.count || ref.checksum != got.checksum) {
-        set_error("autotune: tile_bits %u, block_threads %u, group_hits %u, presieve_groups %u changed the "
-                  "result",
-                  tb, th, gh, g);
+        set_error("autotune: tile_bits %u, block_threads %u, ctas_per_sm %u, group_hits %u, presieve_groups %u "
+                  "changed the result",
+                  tb, th, o.ctas_per_sm, gh, g);
         rc = SIEVE_ERR_CUDA;
         break;
       }
@@ -209,5 +218,166 @@ extern "C" int sieve_autotune_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, in
   if (rc != SIEVE_OK) return rc;
   if (best) *best = best_opt;
   if (best_ms) *best_ms = best_t;
+  return SIEVE_OK;
+}
+
+// ---------------------------------------------------------------- tuning cache
+//
+// The tuned options persist in a small JSON file keyed by (device name, SM
+// count, workload name), one entry per line:
+//   {"sieve_tune_cache": 1, "entries": [
+//   {"device": "...", "sms": 152, "workload": "...", "tile_bits": ..., ..., "ms": ...},
+//   ...
+//   ]}
+// Storing replaces the entry with the same key and keeps the others.
+
+namespace {
+
+bool cache_name_ok(const char *s) {
+  if (!s || !*s || strlen(s) > 200) return false;
+  for (const char *c = s; *c; c++)
+    if (*c == '"' || *c == '\\' || (unsigned char)*c < 0x20) return false;
+  return true;
+}
+
+// The string value of "key": "..." in a one-line entry.
+bool entry_str(const std::string &line, const char *key, std::string *out) {
+  const std::string k = std::string("\"") + key + "\": \"";
+  const size_t a = line.find(k);
+  if (a == std::string::npos) return false;
+  const size_t b = line.find('"', a + k.size());
+  if (b == std::string::npos) return false;
+  *out = line.substr(a + k.size(), b - a - k.size());
+  return true;
+}
+
+bool entry_num(const std::string &line, const char *key, double *out) {
+  const std::string k = std::string("\"") + key + "\": ";
+  const size_t a = line.find(k);
+  if (a == std::string::npos) return false;
+  return sscanf(line.c_str() + a + k.size(), "%lf", out) == 1;
+}
+
+struct CacheEntry {
+  std::string line, device, workload;
+  int sms = 0;
+};
+
+int device_key(const sieve_ctx *ctx, std::string *name) {
+  cudaDeviceProp prop;
+  cudaError_t e = cudaGetDeviceProperties(&prop, ctx->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+  *name = prop.name;
+  for (char &c : *name)
+    if (c == '"' || c == '\\' || (unsigned char)c < 0x20) c = '_';
+  return SIEVE_OK;
+}
+
+std::vector<CacheEntry> read_cache(const char *path) {
+  std::vector<CacheEntry> v;
+  FILE *f = fopen(path, "r");
+  if (!f) return v;
+  char buf[2048];
+  while (fgets(buf, sizeof(buf), f)) {
+    std::string line(buf);
+    while (!line.empty() && (line.back() == '\n' || line.back() == '\r' || line.back() == ',')) line.pop_back();
+    if (line.rfind("{\"device\": ", 0) != 0) continue;
+    CacheEntry en;
+    double sms = 0;
+    if (!entry_str(line, "device", &en.device) || !entry_str(line, "workload", &en.workload) ||
+        !entry_num(line, "sms", &sms))
+      continue;
+    en.sms = (int)sms;
+    en.line = line;
+    v.push_back(en);
+  }
+  fclose(f);
+  return v;
+}
+
+}  // namespace
+
+extern "C" int sieve_tune_cache_store(sieve_ctx *ctx, const char *path, const char *workload, double ms) {
+  if (!ctx || !path || !cache_name_ok(workload)) {
+    set_error("sieve_tune_cache_store: NULL argument, or a workload name that is empty, longer than 200 "
+              "characters or holds a quote, backslash or control character");
+    return SIEVE_ERR_INVALID;
+  }
+  std::string dev;
+  int rc = device_key(ctx, &dev);
+  if (rc != SIEVE_OK) return rc;
+  std::vector<CacheEntry> v = read_cache(path);
+  const sieve_options &o = ctx->opt;
+  char line[1024];
+  snprintf(line, sizeof(line),
+           "{\"device\": \"%s\", \"sms\": %d, \"workload\": \"%s\", \"tile_bits\": %u, \"block_threads\": %u, "
+           "\"ctas_per_sm\": %u, \"group_hits\": %u, \"presieve_groups\": %u, \"batch_tile_bits\": %u, "
+           "\"chunk_primes\": %u, \"ms\": %.6f}",
+           dev.c_str(), ctx->num_sms, workload, o.tile_bits, o.block_threads, o.ctas_per_sm, o.group_hits,
+           o.presieve_groups, o.batch_tile_bits, o.chunk_primes, ms);
+  CacheEntry mine;
+  mine.line = line;
+  mine.device = dev;
+  mine.workload = workload;
+  mine.sms = ctx->num_sms;
+  bool replaced = false;
+  for (CacheEntry &e : v)
+    if (e.device == dev && e.sms == ctx->num_sms && e.workload == workload) {
+      e = mine;
+      replaced = true;
+    }
+  if (!replaced) v.push_back(mine);
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE *f = fopen(tmp.c_str(), "w");
+  if (!f) {
+    set_error("sieve_tune_cache_store: cannot write %s", tmp.c_str());
+    return SIEVE_ERR_INVALID;
+  }
+  fprintf(f, "{\"sieve_tune_cache\": 1, \"entries\": [\n");
+  for (size_t i = 0; i < v.size(); i++) fprintf(f, "%s%s\n", v[i].line.c_str(), i + 1 < v.size() ? "," : "");
+  fprintf(f, "]}\n");
+  const bool ok = fclose(f) == 0 && rename(tmp.c_str(), path) == 0;
+  if (!ok) {
+    set_error("sieve_tune_cache_store: cannot replace %s", path);
+    return SIEVE_ERR_INVALID;
+  }
+  return SIEVE_OK;
+}
+
+extern "C" int sieve_tune_cache_load(sieve_ctx *ctx, const char *path, const char *workload, int *found,
+                                     double *ms) {
+  if (!ctx || !path || !found || !cache_name_ok(workload)) {
+    set_error("sieve_tune_cache_load: NULL argument or bad workload name");
+    return SIEVE_ERR_INVALID;
+  }
+  *found = 0;
+  std::string dev;
+  int rc = device_key(ctx, &dev);
+  if (rc != SIEVE_OK) return rc;
+  for (const CacheEntry &e : read_cache(path)) {
+    if (e.device != dev || e.sms != ctx->num_sms || e.workload != workload) continue;
+    const char *keys[7] = {"tile_bits", "block_threads", "ctas_per_sm", "group_hits", "presieve_groups",
+                           "batch_tile_bits", "chunk_primes"};
+    double v[7];
+    for (int i = 0; i < 7; i++)
+      if (!entry_num(e.line, keys[i], &v[i]) || v[i] < 0 || v[i] > 4294967295.0) {
+        set_error("sieve_tune_cache_load: entry for %s has no valid %s", workload, keys[i]);
+        return SIEVE_ERR_INVALID;
+      }
+    sieve_options o = ctx->opt;
+    o.tile_bits = (uint32_t)v[0];
+    o.block_threads = (uint32_t)v[1];
+    o.ctas_per_sm = (uint32_t)v[2];
+    o.group_hits = (uint32_t)v[3];
+    o.presieve_groups = (uint32_t)v[4];
+    o.batch_tile_bits = (uint32_t)v[5];
+    o.chunk_primes = (uint32_t)v[6];
+    rc = sieve_set_options(ctx, &o);  // validates every field
+    if (rc != SIEVE_OK) return rc;
+    double t = 0;
+    if (ms) *ms = entry_num(e.line, "ms", &t) ? t : 0.0;
+    *found = 1;
+    return SIEVE_OK;
+  }
   return SIEVE_OK;
 }

@@ -629,6 +629,41 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
 
 namespace sieve {
 
+// Tile length and count of a list-mode range of `span` indices per class on
+// `slots` CTA slots with tiles of at most L indices (the rule run_range
+// applies: a range smaller than one full tile per slot gets smaller tiles,
+// down to 1024), and the scratch bytes its per-tile counts, offsets and
+// bitmaps take in the layout of run_range_list_into.
+static size_t list_scratch_need(uint64_t span, uint32_t L, uint64_t slots, uint32_t *L_used, uint64_t *ntiles) {
+  if (span > 0 && span < (uint64_t)L * slots) {
+    const uint64_t want = (span + slots - 1) / slots;
+    uint32_t lw = floor_pow2(want);
+    if (lw < want) lw *= 2;
+    if (lw < 1024) lw = 1024;
+    if (lw < L) L = lw;
+  }
+  const uint64_t n = span ? (span + L - 1) / L : 0;
+  if (L_used) *L_used = L;
+  if (ntiles) *ntiles = n;
+  const size_t off_offsets = align_up((size_t)n * sizeof(uint32_t), 256);
+  const size_t off_bitmap = align_up(off_offsets + ((size_t)n + 1) * sizeof(uint64_t), 256);
+  return off_bitmap + (size_t)n * (L / 32) * sizeof(uint2);
+}
+
+// The widest range whose list scratch fits in `bytes` wherever it starts: the
+// largest span S (indices per class) that fits, found by bisection over the
+// same layout (the need grows with the span), turned into a width: a range of
+// w numbers covers at most floor((w + 9) / 6) indices per class, which is
+// <= S for every w <= 6 S - 4.
+static uint64_t list_scratch_max_width(uint32_t L, uint64_t slots, size_t bytes) {
+  uint64_t lo = 0, hi = (uint64_t)bytes * 8;  // a span of 8 indices per byte never fits
+  while (hi - lo > 1) {
+    const uint64_t mid = lo + (hi - lo) / 2;
+    (list_scratch_need(mid, L, slots, nullptr, nullptr) <= bytes ? lo : hi) = mid;
+  }
+  return lo >= 1 ? 6 * lo - 4 : 0;
+}
+
 // List-mode sieve of [lo, hi) into the device buffer `out` using caller-given
 // scratch and no allocation of any kind: no presieve patterns (every base
 // prime from 5 on is struck), the context's preallocated accumulators, and
@@ -673,24 +708,17 @@ int run_range_list_into(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *out,
   }
   if (ctx->opt.ctas_per_sm && (int)ctx->opt.ctas_per_sm < per_sm) per_sm = (int)ctx->opt.ctas_per_sm;
   const uint64_t slots = (uint64_t)ctx->num_sms * (uint64_t)per_sm;
-  if (span > 0 && span < (uint64_t)L * slots) {
-    const uint64_t want = (span + slots - 1) / slots;
-    uint32_t lw = floor_pow2(want);
-    if (lw < want) lw *= 2;
-    if (lw < 1024) lw = 1024;
-    if (lw < L) L = lw;
-    smem = (size_t)L / 4;
-  }
-  const uint64_t ntiles64 = span ? (span + L - 1) / L : 0;
+  uint64_t ntiles64 = 0;
+  const size_t need = list_scratch_need(span, L, slots, &L, &ntiles64);
+  smem = (size_t)L / 4;
   // scratch layout: [tile counts][offsets][bitmaps]
   const size_t off_offsets = align_up((size_t)ntiles64 * sizeof(uint32_t), 256);
   const size_t off_bitmap = align_up(off_offsets + ((size_t)ntiles64 + 1) * sizeof(uint64_t), 256);
-  const size_t need = off_bitmap + (size_t)ntiles64 * (L / 32) * sizeof(uint2);
   if (ntiles64 > 0xFFFFFFF0ull || need > scratch_bytes) {
-    set_error("range [%llu, %llu) needs %zu bytes of scratch; the fixed scratch holds %zu "
-              "(roughly %llu numbers per call)",
+    set_error("range [%llu, %llu) needs %zu bytes of scratch; the fixed scratch holds %zu, enough for "
+              "ranges of up to %llu numbers with this context's tile length",
               (unsigned long long)lo, (unsigned long long)hi, need, scratch_bytes,
-              (unsigned long long)scratch_bytes * 22);
+              (unsigned long long)list_scratch_max_width(ctx->opt.tile_bits, slots, scratch_bytes));
     return SIEVE_ERR_INVALID;
   }
   const uint32_t ntiles = (uint32_t)ntiles64;

@@ -304,6 +304,9 @@ struct sieve_ctx {
   // growable device staging for list output bound for host memory
   void *d_stage = nullptr;
   size_t stage_bytes = 0;
+  // device address of the fixed scratch array of sieve_range_list_noalloc,
+  // looked up by sieve_create with this context's device current (noalloc.cu)
+  void *noalloc_scratch = nullptr;
   // pinned host staging
   unsigned long long *h_acc = nullptr;
   // phase timing of single-range calls (sieve_set_phase_timing): events
@@ -346,6 +349,12 @@ int ensure_pattern_set_dev(sieve_ctx *ctx, uint32_t logW);
 // Grow the base table to every prime <= new_limit (at most the square of
 // its current limit; api.cu).
 int extend_base_table(sieve_ctx *ctx, uint64_t new_limit);
+
+// Looks up the device address of the fixed no-allocation scratch array on
+// the current device into ctx->noalloc_scratch (noalloc.cu).  Called by
+// sieve_create, so that the array's module is loaded while the context is
+// being made (which allocates anyway), not by a later call that must not.
+int noalloc_setup(sieve_ctx *ctx);
 
 // batch runner lifetime (batch.cu)
 void destroy_batch_runner(BatchRunner *r);

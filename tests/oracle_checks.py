@@ -97,16 +97,16 @@ def check_isqrt(o) -> None:
             assert o.isqrt(n) == math.isqrt(n), n
 
 
-def check_fig1_small(o) -> None:
+def check_primes_upto_small(o) -> None:
     for n in list(range(0, 200)) + [961, 962, 1023, 1024, 4096, 9973, 10000]:
-        got = o.fig1_primes(n).tolist()
+        got = o.primes_upto(n).tolist()
         assert got == brute_primes(2, n + 1), n
 
 
-def check_fig1_published(o) -> None:
+def check_primes_upto_published(o) -> None:
     g = golden("pi_powers_of_ten.json")
     for e in range(1, 9):
-        p = o.fig1_primes(10**e)
+        p = o.primes_upto(10**e)
         assert p.size == g["pi"][str(e)], e
         assert int(p.astype(np.uint64).sum()) == g["sum_below"][str(e)], e
 
@@ -240,7 +240,7 @@ def check_figure2(o) -> None:
 def check_argument_errors(o) -> None:
     import oracle as _o
     assert o.raw_range(5, 4, None, 0, 0, 1, None, None, None, 0, None, 0, None, 0) == _o.ERR_INVALID
-    base = o.fig1_primes(100)
+    base = o.primes_upto(100)
     # a base table that stops short of isqrt(hi - 1) is refused
     assert o.raw_range(0, 10**6, base.ctypes.data, base.size, 100, 1,
                        None, None, None, 0, None, 0, None, 0) == _o.ERR_RANGE
@@ -253,7 +253,7 @@ def check_argument_errors(o) -> None:
     assert n.value == 25
 
 
-ALL_FAST_CHECKS = [check_isqrt, check_fig1_small, check_fig1_published, check_range_small_bruteforce,
+ALL_FAST_CHECKS = [check_isqrt, check_primes_upto_small, check_primes_upto_published, check_range_small_bruteforce,
                    check_range_published, check_high_windows_mr, check_invariants,
                    check_segment_bins, check_mr_vs_td, check_first_class_multiple, check_figure2,
                    check_argument_errors]

@@ -19,21 +19,32 @@ def _need_gpu():
 
 
 def test_count_1e12_histogram():
+    """Every one of the 932 bins and the checksum against the oracle's full
+    run (tests/golden/count_1e12_bins.json, written by
+    tests/golden/make_count_1e12_bins.py from the oracle alone and checked
+    there against OEIS A006880 / A046731), plus sampled blocks against a live
+    oracle run and additivity over two halves."""
     _need_gpu()
     g = C.golden("pi_powers_of_ten.json")
+    full = C.golden("count_1e12_bins.json")
     wl = workloads.COUNT_1E12
+    assert (full["lo"], full["hi_exclusive"], full["seg_width"]) == (wl.lo, wl.hi, wl.seg_width)
     with binding.Sieve(wl.hi) as sv:
         tot, bins = sv.segment_counts(wl.lo, wl.hi, wl.seg_width)
         assert len(bins) == 932
-        assert tot.count == g["pi"]["12"]
-        assert int(bins.sum()) == tot.count
+        assert tot.count == g["pi"]["12"] == full["count"]
+        assert tot.checksum == full["checksum_mod_2_64"] == full["sum_below_1e12"] % 2**64
+        np.testing.assert_array_equal(bins, np.array(full["bins"], dtype=np.uint64))
+        # the count-only path (no bins) and the host-output path agree with it
+        r = sv.range_count(wl.lo, wl.hi)
+        assert (r.count, r.checksum) == (tot.count, tot.checksum)
         # additivity of the checksum over two halves
         mid = 6 * 10**11 + 12345
         a = sv.range_count(wl.lo, mid)
         b = sv.range_count(mid, wl.hi)
         assert a.count + b.count == tot.count
         assert (a.checksum + b.checksum) % 2**64 == tot.checksum
-        # sampled blocks against the oracle (first, a middle one, two random, the partial last)
+        # sampled blocks against a live oracle run (first, a middle one, two random, the partial last)
         base = oracle.base_table(10**6)
         rng = np.random.default_rng(12)
         picks = sorted({0, 465, len(bins) - 1} | {int(x) for x in rng.integers(1, len(bins) - 1, size=2)})

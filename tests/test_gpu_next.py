@@ -25,7 +25,7 @@ def test_first_million_primes(torch):
     g = C.golden("pi_powers_of_ten.json")
     assert got.size == 10**6
     assert int(got[-1]) == 15485863  # the millionth prime
-    want = oracle.fig1_primes(15485863).astype(np.uint64)
+    want = oracle.primes_upto(15485863).astype(np.uint64)
     np.testing.assert_array_equal(got, want)
     assert int(np.searchsorted(got, 10**6, side="right")) == g["pi"]["6"]
 

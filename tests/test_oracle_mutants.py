@@ -18,8 +18,8 @@ MUTANTS = {
     "no_square_start": ("      if (m < p * p) m = p * p;\n", ""),
     # base primes needed up to isqrt(hi - 1): stop one too early
     "base_cutoff_off_by_one": ("if (p * p > e - 1) break;", "if (p * p >= e - 1) break;"),
-    # Figure 1 loop bound i*i <= n written as i*i < n
-    "fig1_strict_bound": ("for (uint64_t i = 2; i * i <= n; i++) {", "for (uint64_t i = 2; i * i < n; i++) {"),
+    # primes <= n: the crossing-off primes must reach isqrt(n), not stop one short
+    "upto_base_bound_short": ("  const uint64_t r = oracle_isqrt(n);\n", "  const uint64_t r = oracle_isqrt(n) - 1;\n"),
     # keeps 0 and 1 as primes
     "keeps_one": ("if (!seg[i] || v < 2) continue;", "if (!seg[i] || v < 1) continue;"),
     # bins counted from lo instead of from multiples of the width
@@ -34,7 +34,7 @@ MUTANTS = {
 }
 
 # checks cheap enough to run on every mutant (the 1e9 / 1e10 runs are skipped)
-CHECKS = [C.check_isqrt, C.check_fig1_small, C.check_range_small_bruteforce,
+CHECKS = [C.check_isqrt, C.check_primes_upto_small, C.check_range_small_bruteforce,
           C.check_invariants, C.check_segment_bins, C.check_mr_vs_td,
           C.check_first_class_multiple, C.check_figure2]
 
