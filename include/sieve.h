@@ -95,6 +95,16 @@ typedef struct {
                               length, times its tiles, reach this number is "merged": those
                               primes are applied by strip items of at most this many primes,
                               each striking the query's bitmap in global memory             */
+  uint32_t bucket_threshold; /* single ranges: base primes above bucket_threshold x tile_bits go
+                              through the bucket sieve (located once per wave of tiles, their hits
+                              sorted into per-tile buckets that each tile drains) when they are
+                              many and each hits a tile rarely; 0 = off (every prime is located
+                              in every tile); at most 64                                     */
+  uint32_t bucket_wave;    /* bucket sieve: tiles per CTA in one wave (1..16)                  */
+  uint32_t bucket_scatter; /* bucket sieve: 1 = direct scatter (each hit stored at once), 2 =
+                              sorted scatter (a round's hits sorted by tile in shared memory,
+                              written in runs), 0 = direct while a wave's entries fit in L2,
+                              else sorted with waves of at least 4 tiles per CTA              */
   uint32_t reserved[1];
 } sieve_options;
 
@@ -247,7 +257,10 @@ int sieve_range_each(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, con
  *   sieve_autotune_range: tile_bits {2^18, 2^19} x block_threads {512, 1024}
  *     x ctas_per_sm {0, 1, 2} (512 threads only) x group_hits {3, 4, 5, 6, 8}
  *     x presieve_groups {5, 6, 7, 8} on the count of [lo, hi) (a sample of the
- *     ranges to come; every candidate sieves it reps + 1 times). */
+ *     ranges to come; every candidate sieves it reps + 1 times); then, when
+ *     the range's large primes can use the bucket sieve, bucket_threshold
+ *     {0, 2, 4, 8, 16} x bucket_wave {1, 4} x bucket_scatter {1, 2} with the
+ *     winner's other settings. */
 int sieve_autotune_batch(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, const uint8_t *mode, size_t nq,
                          int reps, sieve_options *best, double *best_ms);
 int sieve_autotune_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, int reps, sieve_options *best,
@@ -394,6 +407,7 @@ typedef struct {
   uint64_t tiles;     /* tiles the tile kernel sieved */
   uint64_t tile_len;  /* indices per residue class per tile */
   uint64_t listed;    /* list mode: primes the compaction wrote */
+  uint64_t bucket_waves; /* waves of the bucket sieve (0: not used) */
 } sieve_phase_times;
 
 /* enable != 0 turns phase timing on (creating the events), 0 turns it off.

@@ -51,13 +51,16 @@ class Options(ctypes.Structure):
     _fields_ = [("tile_bits", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
                 ("ctas_per_sm", ctypes.c_uint32), ("group_hits", ctypes.c_uint32),
                 ("presieve_groups", ctypes.c_uint32), ("batch_tile_bits", ctypes.c_uint32),
-                ("chunk_primes", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 1)]
+                ("chunk_primes", ctypes.c_uint32), ("bucket_threshold", ctypes.c_uint32),
+                ("bucket_wave", ctypes.c_uint32), ("bucket_scatter", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 1)]
 
     def as_dict(self) -> dict:
         return {"tile_bits": self.tile_bits, "block_threads": self.block_threads,
                 "ctas_per_sm": self.ctas_per_sm, "group_hits": self.group_hits,
                 "presieve_groups": self.presieve_groups, "batch_tile_bits": self.batch_tile_bits,
-                "chunk_primes": self.chunk_primes}
+                "chunk_primes": self.chunk_primes, "bucket_threshold": self.bucket_threshold,
+                "bucket_wave": self.bucket_wave, "bucket_scatter": self.bucket_scatter}
 
 
 class ServerConfig(ctypes.Structure):
@@ -67,7 +70,8 @@ class ServerConfig(ctypes.Structure):
 
 class PhaseTimes(ctypes.Structure):
     _fields_ = [("sieve_ms", ctypes.c_double), ("scan_ms", ctypes.c_double), ("compact_ms", ctypes.c_double),
-                ("tiles", ctypes.c_uint64), ("tile_len", ctypes.c_uint64), ("listed", ctypes.c_uint64)]
+                ("tiles", ctypes.c_uint64), ("tile_len", ctypes.c_uint64), ("listed", ctypes.c_uint64),
+                ("bucket_waves", ctypes.c_uint64)]
 
 
 class ServerStats(ctypes.Structure):

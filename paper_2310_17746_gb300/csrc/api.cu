@@ -217,6 +217,7 @@ static void free_ctx(sieve_ctx *c) {
   cudaFree(c->d_acc);
   cudaFree(c->d_scratch);
   cudaFree(c->d_stage);
+  cudaFree(c->d_bucket);
   if (c->h_acc) cudaFreeHost(c->h_acc);
   for (cudaEvent_t &e : c->ph_ev)
     if (e) cudaEventDestroy(e);
@@ -233,6 +234,9 @@ static sieve_options default_options() {
   o.presieve_groups = 7;  // patterns to 109
   o.batch_tile_bits = 1u << 18;
   o.chunk_primes = 1u << 15;
+  o.bucket_threshold = 4;  // primes above 4 L through the bucket sieve, where it pays (measured best of 1..16)
+  o.bucket_wave = 1;
+  o.bucket_scatter = 0;    // direct or sorted scatter by the size of a wave's buckets
   return o;
 }
 
@@ -265,6 +269,18 @@ static int validate_options(const sieve_ctx *c, const sieve_options &o) {
   }
   if (o.chunk_primes < 1024) {
     set_error("chunk_primes must be >= 1024");
+    return SIEVE_ERR_INVALID;
+  }
+  if (o.bucket_threshold > 64) {
+    set_error("bucket_threshold must be in [0, 64]");
+    return SIEVE_ERR_INVALID;
+  }
+  if (o.bucket_scatter > 2) {
+    set_error("bucket_scatter must be 0 (automatic), 1 (direct) or 2 (sorted)");
+    return SIEVE_ERR_INVALID;
+  }
+  if (o.bucket_wave < 1 || o.bucket_wave > 16) {
+    set_error("bucket_wave must be in [1, 16]");
     return SIEVE_ERR_INVALID;
   }
   if (o.presieve_groups > (uint32_t)kMaxPresieveGroups) {
@@ -683,7 +699,7 @@ extern "C" int sieve_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, int mode, s
   rq.out_on_device = (flags & SIEVE_OUT_DEVICE) != 0;
   rq.total = cnt;
   rq.async = mode == SIEVE_COUNT && (flags & SIEVE_OUT_DEVICE) && (flags & SIEVE_ASYNC);
-  if (!rq.async && strips_pay_off(ctx, lo, hi)) {
+  if (!rq.async && !range_prefers_buckets(ctx, lo, hi) && strips_pay_off(ctx, lo, hi)) {
     // a range far up: run it as a one-query batch, whose planner locates the
     // primes above the tile length once for the whole range (strips) instead
     // of once per tile

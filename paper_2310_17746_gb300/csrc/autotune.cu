@@ -144,6 +144,49 @@ extern "C" int sieve_autotune_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, in
   sieve_options best_opt = orig;
   double best_t = 1e300;
   sieve_count_result ref{0, 0}, got{0, 0};
+  bool have_ref = false;
+  // times each candidate (reps runs after an untimed one) and keeps the
+  // fastest; every candidate's result must equal the first one's
+  auto try_all = [&](const std::vector<sieve_options> &cand) {
+    cudaError_t e;
+    for (const sieve_options &o : cand) {
+      if (sieve_set_options(ctx, &o) != SIEVE_OK) continue;
+      std::vector<double> ts;
+      for (int r = 0; r <= reps && rc == SIEVE_OK; r++) {
+        if ((e = cudaEventRecord(ev.a, ctx->stream)) != cudaSuccess) rc = cuda_fail(e, "cudaEventRecord");
+        if (rc == SIEVE_OK)
+          rc = sieve_range(ctx, lo, hi, SIEVE_COUNT, d_tot, nullptr, 0, nullptr, SIEVE_OUT_DEVICE | SIEVE_ASYNC);
+        if (rc == SIEVE_OK && (e = cudaEventRecord(ev.b, ctx->stream)) != cudaSuccess)
+          rc = cuda_fail(e, "cudaEventRecord");
+        if (rc == SIEVE_OK && (e = cudaEventSynchronize(ev.b)) != cudaSuccess)
+          rc = cuda_fail(e, "cudaEventSynchronize");
+        float ms = 0.f;
+        if (rc == SIEVE_OK) cudaEventElapsedTime(&ms, ev.a, ev.b);
+        if (r > 0) ts.push_back(ms);
+      }
+      if (rc != SIEVE_OK) return;
+      if ((e = cudaMemcpy(&got, d_tot, sizeof(got), cudaMemcpyDeviceToHost)) != cudaSuccess) {
+        rc = cuda_fail(e, "cudaMemcpy");
+        return;
+      }
+      if (!have_ref) {
+        ref = got;
+        have_ref = true;
+      } else if (ref.count != got.count || ref.checksum != got.checksum) {
+        set_error("autotune: tile_bits %u, block_threads %u, ctas_per_sm %u, group_hits %u, presieve_groups %u, "
+                  "bucket_threshold %u, bucket_wave %u, bucket_scatter %u changed the result",
+                  o.tile_bits, o.block_threads, o.ctas_per_sm, o.group_hits, o.presieve_groups,
+                  o.bucket_threshold, o.bucket_wave, o.bucket_scatter);
+        rc = SIEVE_ERR_CUDA;
+        return;
+      }
+      const double t = median(ts);
+      if (t < best_t) {
+        best_t = t;
+        best_opt = o;
+      }
+    }
+  };
   do {
     cudaError_t e;
     if ((e = cudaMalloc(&d_tot, sizeof(sieve_count_result))) != cudaSuccess ||
@@ -151,8 +194,8 @@ extern "C" int sieve_autotune_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, in
       rc = cuda_fail(e, "autotune allocation");
       break;
     }
-    // tile length (Section 5's array size), threads per CTA, CTAs per SM, the
-    // warp/lane split and the presieve depth
+    // stage 1: tile length (Section 5's array size), threads per CTA, CTAs per
+    // SM, the warp/lane split and the presieve depth
     const uint32_t tiles[] = {1u << 18, 1u << 19};
     const uint32_t threads[] = {512, 1024};
     const uint32_t ctas[] = {0, 1, 2};
@@ -174,43 +217,31 @@ extern "C" int sieve_autotune_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, in
               cand.push_back(o);
             }
         }
-    bool have_ref = false;
-    for (const sieve_options &o : cand) {
-      const uint32_t tb = o.tile_bits, th = o.block_threads, gh = o.group_hits, g = o.presieve_groups;
-      if (sieve_set_options(ctx, &o) != SIEVE_OK) continue;
-      std::vector<double> ts;
-      for (int r = 0; r <= reps && rc == SIEVE_OK; r++) {
-        if ((e = cudaEventRecord(ev.a, ctx->stream)) != cudaSuccess) rc = cuda_fail(e, "cudaEventRecord");
-        if (rc == SIEVE_OK)
-          rc = sieve_range(ctx, lo, hi, SIEVE_COUNT, d_tot, nullptr, 0, nullptr, SIEVE_OUT_DEVICE | SIEVE_ASYNC);
-        if (rc == SIEVE_OK && (e = cudaEventRecord(ev.b, ctx->stream)) != cudaSuccess)
-          rc = cuda_fail(e, "cudaEventRecord");
-        if (rc == SIEVE_OK && (e = cudaEventSynchronize(ev.b)) != cudaSuccess)
-          rc = cuda_fail(e, "cudaEventSynchronize");
-        float ms = 0.f;
-        if (rc == SIEVE_OK) cudaEventElapsedTime(&ms, ev.a, ev.b);
-        if (r > 0) ts.push_back(ms);
-      }
-      if (rc != SIEVE_OK) break;
-      if ((e = cudaMemcpy(&got, d_tot, sizeof(got), cudaMemcpyDeviceToHost)) != cudaSuccess) {
-        rc = cuda_fail(e, "cudaMemcpy");
-        break;
-      }
-      if (!have_ref) {
-        ref = got;
-        have_ref = true;
-      } else if (ref.count != got.count || ref.checksum != got.checksum) {
-        set_error("autotune: tile_bits %u, block_threads %u, ctas_per_sm %u, group_hits %u, presieve_groups %u "
-                  "changed the result",
-                  tb, th, o.ctas_per_sm, gh, g);
-        rc = SIEVE_ERR_CUDA;
-        break;
-      }
-      const double t = median(ts);
-      if (t < best_t) {
-        best_t = t;
-        best_opt = o;
-      }
+    try_all(cand);
+    if (rc != SIEVE_OK) break;
+    // stage 2, for ranges whose large primes can go through the bucket sieve:
+    // the large-prime threshold (off, or 2..16 tile lengths), the wave size
+    // and the scatter kind, with the stage-1 winner's other settings
+    sieve_options probe = best_opt;
+    probe.bucket_threshold = 2;
+    probe.bucket_scatter = 0;
+    ctx->opt = probe;
+    const bool buckets = range_prefers_buckets(ctx, lo, hi);
+    if (buckets) {
+      std::vector<sieve_options> bc;
+      sieve_options off = best_opt;
+      off.bucket_threshold = 0;
+      bc.push_back(off);
+      for (uint32_t thr : {2u, 4u, 8u, 16u})
+        for (uint32_t wv : {1u, 4u})
+          for (uint32_t sc : {1u, 2u}) {
+            sieve_options o = best_opt;
+            o.bucket_threshold = thr;
+            o.bucket_wave = wv;
+            o.bucket_scatter = sc;
+            bc.push_back(o);
+          }
+      try_all(bc);
     }
   } while (0);
   cudaFree(d_tot);
@@ -312,9 +343,11 @@ extern "C" int sieve_tune_cache_store(sieve_ctx *ctx, const char *path, const ch
   snprintf(line, sizeof(line),
            "{\"device\": \"%s\", \"sms\": %d, \"workload\": \"%s\", \"tile_bits\": %u, \"block_threads\": %u, "
            "\"ctas_per_sm\": %u, \"group_hits\": %u, \"presieve_groups\": %u, \"batch_tile_bits\": %u, "
-           "\"chunk_primes\": %u, \"ms\": %.6f}",
+           "\"chunk_primes\": %u, \"bucket_threshold\": %u, \"bucket_wave\": %u, \"bucket_scatter\": %u, "
+           "\"ms\": %.6f}",
            dev.c_str(), ctx->num_sms, workload, o.tile_bits, o.block_threads, o.ctas_per_sm, o.group_hits,
-           o.presieve_groups, o.batch_tile_bits, o.chunk_primes, ms);
+           o.presieve_groups, o.batch_tile_bits, o.chunk_primes, o.bucket_threshold, o.bucket_wave,
+           o.bucket_scatter, ms);
   CacheEntry mine;
   mine.line = line;
   mine.device = dev;
@@ -372,6 +405,11 @@ extern "C" int sieve_tune_cache_load(sieve_ctx *ctx, const char *path, const cha
     o.presieve_groups = (uint32_t)v[4];
     o.batch_tile_bits = (uint32_t)v[5];
     o.chunk_primes = (uint32_t)v[6];
+    double bt = 0, bw = 0;  // entries written before the bucket sieve existed lack these
+    if (entry_num(e.line, "bucket_threshold", &bt) && bt >= 0 && bt <= 64) o.bucket_threshold = (uint32_t)bt;
+    if (entry_num(e.line, "bucket_wave", &bw) && bw >= 1 && bw <= 16) o.bucket_wave = (uint32_t)bw;
+    double bs = 0;
+    if (entry_num(e.line, "bucket_scatter", &bs) && bs >= 0 && bs <= 2) o.bucket_scatter = (uint32_t)bs;
     rc = sieve_set_options(ctx, &o);  // validates every field
     if (rc != SIEVE_OK) return rc;
     double t = 0;

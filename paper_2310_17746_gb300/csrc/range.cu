@@ -9,8 +9,11 @@
 // checksum and per-segment counts (count mode) or bitmap write-out (list mode,
 // followed by a scan of per-tile counts and a compaction kernel).
 #include <algorithm>
+#include <cmath>
+#include <cstdlib>
 #include <cstring>
 
+#include "bucket.cuh"
 #include "tile.cuh"
 
 namespace sieve {
@@ -42,8 +45,13 @@ struct RangeKernelParams {
   uint2 *bitmap;            // per tile L/32 (class-1 word, class-5 word) pairs
 };
 
-template <int BLOCK, bool LIST>
-__global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const RangeKernelParams p) {
+// BUCKET: the launch sieves the tiles of one bucket wave, [b.t_begin,
+// b.t_begin + b.ntl); the primes with table index >= b.i_large are applied by
+// draining the wave's buckets (bucket.cuh) instead of being located in every
+// tile.  Without BUCKET the launch sieves every tile and b is unused.
+template <int BLOCK, bool LIST, bool BUCKET>
+__global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const RangeKernelParams p,
+                                                                          const BucketParams b) {
   constexpr int NWARPS = BLOCK / 32;
   extern __shared__ uint32_t smem[];
   const uint32_t W = p.L / 32;
@@ -55,16 +63,19 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
   __shared__ uint64_t sh_bin0;
   __shared__ int64_t sh_t1, sh_t5;
   __shared__ int sh_has_boundary;
+  __shared__ uint32_t sh_overflow;
   __shared__ uint64_t red[3 * NWARPS];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t t_begin = BUCKET ? b.t_begin : 0u;
+  const uint32_t t_end = BUCKET ? b.t_begin + b.ntl : p.ntiles;
   uint32_t np_prev = 0;  // warp 0: the previous tile's prime count
   // the pattern offsets K0 mod period: computed once per tile by a few
   // threads (for the next tile at the end of this one), not by every thread
-  if (threadIdx.x < (uint32_t)p.npat && blockIdx.x < p.ntiles)
-    sh_poff[threadIdx.x] = pattern_offset(p.k_begin + (uint64_t)blockIdx.x * p.L, p.pd[threadIdx.x]);
+  if (threadIdx.x < (uint32_t)p.npat && t_begin + blockIdx.x < t_end)
+    sh_poff[threadIdx.x] = pattern_offset(p.k_begin + (uint64_t)(t_begin + blockIdx.x) * p.L, p.pd[threadIdx.x]);
   __syncthreads();
 
-  for (uint32_t t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
+  for (uint32_t t = t_begin + blockIdx.x; t < t_end; t += gridDim.x) {
     const uint64_t K0 = p.k_begin + (uint64_t)t * p.L;
     const uint64_t left = p.k_end - K0;
     TileGeom tg;
@@ -91,6 +102,10 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
         sh_allsq = Plast * Plast <= B && Plast < 0x80000000ull;
         sh_next = p.i_first;
         sh_has_boundary = 0;
+        if (BUCKET) {  // read and re-arm the tile's overflow flag
+          sh_overflow = b.overflow[t - t_begin];
+          if (sh_overflow) b.overflow[t - t_begin] = 0;
+        }
         if (p.seg_width) {
           const uint64_t v0 = B > p.lo ? B : p.lo;
           const uint64_t sg = v0 / p.seg_width;
@@ -109,8 +124,19 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
     warp_band_starts<BLOCK>(starts, B, tg.len, p.primes, p.magic, p.cinv, p.i_first, p.i_split);
     __syncthreads();
 
-    strike_primes<BLOCK>(s1, s5, B, tg, p.primes, p.magic, p.cinv, starts, p.i_first, p.i_split, sh_np,
-                         sh_allsq != 0, &sh_next, K0);
+    if (BUCKET) {
+      // primes below i_large as usual, the rest from the buckets; a tile whose
+      // buckets overflowed also locates the large primes itself (a strike
+      // applied twice is harmless)
+      strike_primes<BLOCK>(s1, s5, B, tg, p.primes, p.magic, p.cinv, starts, p.i_first, p.i_split, sh_np,
+                           sh_allsq != 0, &sh_next, K0, b.i_large);
+      bucket_drain<BLOCK>(s1, s5, tg, b, t - t_begin);
+      if (sh_overflow && sh_np > b.i_large)
+        strike_lane_band<BLOCK>(s1, s5, B, tg, p.primes, p.magic, p.cinv, b.i_large, sh_np, sh_allsq != 0, K0);
+    } else {
+      strike_primes<BLOCK>(s1, s5, B, tg, p.primes, p.magic, p.cinv, starts, p.i_first, p.i_split, sh_np,
+                           sh_allsq != 0, &sh_next, K0);
+    }
     __syncthreads();
 
     // a full tile above the presieved primes and inside [lo, hi) needs no
@@ -191,7 +217,7 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
       }
     }
     const uint32_t tn = t + gridDim.x;  // the next tile's pattern offsets (a warp other than thread 0's)
-    if (threadIdx.x >= 32 && threadIdx.x < 32 + (uint32_t)p.npat && tn < p.ntiles)
+    if (threadIdx.x >= 32 && threadIdx.x < 32 + (uint32_t)p.npat && tn < t_end)
       sh_poff[threadIdx.x - 32] = pattern_offset(p.k_begin + (uint64_t)tn * p.L, p.pd[threadIdx.x - 32]);
     __syncthreads();
   }
@@ -293,11 +319,21 @@ static size_t compact_smem_bytes(uint32_t L) {
 namespace {
 
 template <int BLOCK>
-int launch_range_tiles(sieve_ctx *ctx, const RangeKernelParams &p, bool list, int grid, size_t smem) {
-  if (list)
-    range_tiles_kernel<BLOCK, true><<<grid, BLOCK, smem, ctx->stream>>>(p);
-  else
-    range_tiles_kernel<BLOCK, false><<<grid, BLOCK, smem, ctx->stream>>>(p);
+int launch_range_tiles(sieve_ctx *ctx, const RangeKernelParams &p, const BucketParams *b, bool list, int grid,
+                       size_t smem) {
+  BucketParams none;
+  memset(&none, 0, sizeof(none));
+  if (b) {
+    if (list)
+      range_tiles_kernel<BLOCK, true, true><<<grid, BLOCK, smem, ctx->stream>>>(p, *b);
+    else
+      range_tiles_kernel<BLOCK, false, true><<<grid, BLOCK, smem, ctx->stream>>>(p, *b);
+  } else {
+    if (list)
+      range_tiles_kernel<BLOCK, true, false><<<grid, BLOCK, smem, ctx->stream>>>(p, none);
+    else
+      range_tiles_kernel<BLOCK, false, false><<<grid, BLOCK, smem, ctx->stream>>>(p, none);
+  }
   ctx->launches++;
   SIEVE_CUDA_TRY(cudaGetLastError());
   return SIEVE_OK;
@@ -305,19 +341,23 @@ int launch_range_tiles(sieve_ctx *ctx, const RangeKernelParams &p, bool list, in
 
 template <int BLOCK>
 int occupancy(int *blocks, bool list, size_t smem) {
-  cudaError_t e = list ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, range_tiles_kernel<BLOCK, true>,
-                                                                       BLOCK, smem)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, range_tiles_kernel<BLOCK, false>,
-                                                                       BLOCK, smem);
+  cudaError_t e = list ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                             blocks, range_tiles_kernel<BLOCK, true, false>, BLOCK, smem)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                             blocks, range_tiles_kernel<BLOCK, false, false>, BLOCK, smem);
   SIEVE_CUDA_TRY(e);
   return SIEVE_OK;
 }
 
 template <int BLOCK>
 int set_smem_attr(int bytes) {
-  SIEVE_CUDA_TRY(cudaFuncSetAttribute(range_tiles_kernel<BLOCK, true>,
+  SIEVE_CUDA_TRY(cudaFuncSetAttribute(range_tiles_kernel<BLOCK, true, false>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  SIEVE_CUDA_TRY(cudaFuncSetAttribute(range_tiles_kernel<BLOCK, false>,
+  SIEVE_CUDA_TRY(cudaFuncSetAttribute(range_tiles_kernel<BLOCK, false, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  SIEVE_CUDA_TRY(cudaFuncSetAttribute(range_tiles_kernel<BLOCK, true, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  SIEVE_CUDA_TRY(cudaFuncSetAttribute(range_tiles_kernel<BLOCK, false, true>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   return SIEVE_OK;
 }
@@ -330,11 +370,12 @@ int dispatch_occupancy(int threads, int *blocks, bool list, size_t smem) {
   }
 }
 
-int dispatch_launch(sieve_ctx *ctx, int threads, const RangeKernelParams &p, bool list, int grid, size_t smem) {
+int dispatch_launch(sieve_ctx *ctx, int threads, const RangeKernelParams &p, bool list, int grid, size_t smem,
+                    const BucketParams *b = nullptr) {
   switch (threads) {
-    case 256: return launch_range_tiles<256>(ctx, p, list, grid, smem);
-    case 512: return launch_range_tiles<512>(ctx, p, list, grid, smem);
-    default: return launch_range_tiles<1024>(ctx, p, list, grid, smem);
+    case 256: return launch_range_tiles<256>(ctx, p, b, list, grid, smem);
+    case 512: return launch_range_tiles<512>(ctx, p, b, list, grid, smem);
+    default: return launch_range_tiles<1024>(ctx, p, b, list, grid, smem);
   }
 }
 
@@ -370,6 +411,198 @@ static uint32_t log2u(uint32_t x) {
   uint32_t r = 0;
   while ((1u << r) < x) r++;
   return r;
+}
+
+// Tile geometry of a single-range call (shared by run_range and the routing
+// decision of sieve_range): tile length L (tile_bits, at most one segment
+// boundary per tile when per-segment counts are asked for, smaller tiles when
+// the range gives fewer than one full tile per CTA slot), tile count, grid,
+// base primes needed and the warp/lane split (a warp takes a prime while it
+// has >= group_hits hits per lane in a tile, i.e. P <= L / (32 group_hits)),
+// and the dynamic shared memory of the tile kernel.
+struct RangeGeom {
+  uint64_t k_begin, k_end;  // class indices [k_begin, k_end) cover [lo, hi)
+  uint32_t L, ntiles, np, i_first, i_split;
+  int threads, grid;
+  size_t smem;
+};
+
+static int range_geometry(const sieve_ctx *ctx, const DeviceTable &table, uint64_t lo, uint64_t hi,
+                          uint64_t seg_width, bool list, RangeGeom *g) {
+  g->k_begin = lo / 6;
+  g->k_end = (hi + 4) / 6;  // ceil((hi - 1) / 6)
+  const uint64_t span = g->k_end > g->k_begin ? g->k_end - g->k_begin : 0;
+  g->threads = (int)ctx->opt.block_threads;
+  uint32_t L = ctx->opt.tile_bits;
+  if (seg_width) {  // at most one segment boundary per tile: 6 L <= seg_width
+    const uint32_t lw = floor_pow2(seg_width / 6);
+    if (lw < L) L = lw;
+  }
+  int per_sm = 0;
+  int rc = dispatch_occupancy(g->threads, &per_sm, list, (size_t)L / 4);
+  if (rc != SIEVE_OK) return rc;
+  if (per_sm < 1) {
+    set_error("tile of %u bits does not fit on an SM", L);
+    return SIEVE_ERR_INVALID;
+  }
+  if (ctx->opt.ctas_per_sm && (int)ctx->opt.ctas_per_sm < per_sm) per_sm = (int)ctx->opt.ctas_per_sm;
+  const uint64_t slots = (uint64_t)ctx->num_sms * (uint64_t)per_sm;
+  // small ranges: shrink tiles so that every CTA slot gets work
+  if (span > 0 && span < (uint64_t)L * slots) {
+    const uint64_t want = (span + slots - 1) / slots;
+    uint32_t lw = floor_pow2(want);
+    if (lw < want) lw *= 2;
+    if (lw < 1024) lw = 1024;
+    if (lw < L) L = lw;
+  }
+  const uint64_t ntiles64 = span ? (span + L - 1) / L : 0;
+  if (ntiles64 > 0xFFFFFFF0ull) {
+    set_error("range needs too many tiles");
+    return SIEVE_ERR_INVALID;
+  }
+  g->L = L;
+  g->ntiles = (uint32_t)ntiles64;
+  g->grid = (int)std::min<uint64_t>(g->ntiles ? g->ntiles : 1, slots);
+  const uint64_t s = hi >= 2 ? isqrt_u64(hi - 1) : 0;
+  g->np = host_prime_count_le_table(table, s);
+  const uint64_t gmax = L / (32ull * std::max<uint32_t>(1u, ctx->opt.group_hits));
+  g->i_first = first_struck_prime_index((int)ctx->opt.presieve_groups);
+  g->i_split = std::min(host_prime_count_le_table(table, gmax), g->np);
+  if (g->i_split < g->i_first) g->i_split = g->i_first;
+  g->smem = (size_t)L / 4 + (size_t)(g->i_split - g->i_first) * sizeof(uint2);
+  if (g->smem > (size_t)ctx->smem_optin) {
+    set_error("tile of %u bits with %u warp-band primes needs %zu bytes of shared memory", L,
+              g->i_split - g->i_first, g->smem);
+    return SIEVE_ERR_INVALID;
+  }
+  return SIEVE_OK;
+}
+
+constexpr int kScatterBlock = 512;  // threads of bucket_scatter_kernel
+constexpr int kScatterHits = 16;    // hits per thread per round
+
+// Upper bound on the sum of 1/p over the primes p in (a, b], a >= 286: with
+// Rosser & Schoenfeld's bound |sum_{p <= x} 1/p - ln ln x - B| < 1 / (2 ln^2 x)
+// ("Approximate formulas for some functions of prime numbers", 1962, (3.18)).
+static double prime_reciprocal_sum_bound(double a, double b) {
+  if (b <= a) return 0.0;
+  const double la = std::log(a), lb = std::log(b);
+  return std::log(lb) - std::log(la) + 0.5 / (la * la) + 0.5 / (lb * lb);
+}
+
+// Which scatter kernel and how many bytes of bucket entries a wave of one
+// tile per CTA holds, above which the sorted scatter (coalesced writes, waves
+// of at least four tiles per CTA) beats the direct one (measured: the direct
+// scatter's scattered stores are cheap while the wave's entries stay in L2).
+constexpr double kBucketDirectMaxBytes = 96e6;
+
+static size_t scatter_smem(bool sorted, uint32_t ntl) {
+  return sorted ? bucket_scatter_smem(kScatterBlock, kScatterHits, ntl) : (size_t)ntl * sizeof(uint32_t);
+}
+
+// Scatter CTAs per SM for a wave of ntl tiles (occupancy of the scatter kernel).
+static int scatter_ctas_per_sm(bool sorted, uint32_t ntl) {
+  int blocks = 0;
+  const size_t smem = scatter_smem(sorted, ntl);
+  const void *fn = sorted ? (const void *)bucket_scatter_kernel<kScatterBlock, kScatterHits>
+                          : (const void *)bucket_scatter_direct_kernel<kScatterBlock>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, kScatterBlock, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return blocks;
+}
+
+// Whether a range's large primes go through the bucket sieve, and its layout:
+// the primes above bucket_threshold x L (table indices [i_large, np)) when
+// there are many of them and each hits a tile's two classes rarely.  The mean
+// hits per prime per tile, h = 2 L sum(1/p) / N, must stay below
+// kBucketMaxHits: a bucket entry costs about four per-tile locations
+// (measured break-even near h = 0.28 at [1e14, 1e14 + 1e11)).  Waves of
+// bucket_wave x grid tiles (at least four per CTA for the sorted scatter);
+// sub-bucket capacity from the expected hits per (tile, scatter CTA) with a
+// margin of six standard deviations (overflow is handled by the tile, see
+// bucket.cuh).  With plan == nullptr only the decision is made (no device
+// calls); else *plan receives the layout (without t_begin / ntl).
+struct BucketPlan {
+  BucketParams b;
+  uint32_t wave;
+  bool sorted;
+};
+
+static bool plan_buckets(const sieve_ctx *ctx, const DeviceTable &table, const RangeGeom &g, BucketPlan *plan) {
+  constexpr uint32_t kBucketMinPrimes = 8192;
+  constexpr double kBucketMaxHits = 0.25;
+  const sieve_options &o = ctx->opt;
+  if (!o.bucket_threshold || g.ntiles < 2 || g.np == 0) return false;
+  const uint64_t T = (uint64_t)o.bucket_threshold * g.L;
+  uint32_t i_large = host_prime_count_le_table(table, T);
+  if (i_large < g.i_split) i_large = g.i_split;
+  if (g.np < i_large + kBucketMinPrimes) return false;
+  const uint32_t Pmax = table.host_primes[g.np - 1];
+  if (Pmax >= 0x80000000u) return false;
+  const uint32_t Plo = table.host_primes[i_large];
+  const double S = prime_reciprocal_sum_bound(std::max<double>(Plo - 1, 286.0), (double)Pmax);
+  const double n_large = (double)(g.np - i_large);
+  const double e_tile = 2.0 * g.L * S;  // expected bucket entries per tile
+  if (e_tile / n_large > kBucketMaxHits) return false;
+  if (!plan) return true;
+  const bool sorted = o.bucket_scatter == 2 ||
+                      (o.bucket_scatter == 0 && e_tile * g.grid * sizeof(uint32_t) > kBucketDirectMaxBytes);
+  uint32_t per_cta = std::max<uint32_t>(1u, o.bucket_wave);
+  if (sorted && o.bucket_scatter == 0) per_cta = std::max<uint32_t>(per_cta, 4u);
+  uint64_t ntl = (uint64_t)per_cta * g.grid;
+  ntl = std::min<uint64_t>(ntl, g.ntiles);
+  ntl = std::min<uint64_t>(ntl, kBucketMaxWaveTiles - 1);
+  while (ntl > 1 && ntl * g.L >= (1ull << 31)) ntl--;
+  const int scatter_ctas = scatter_ctas_per_sm(sorted, (uint32_t)ntl) * ctx->num_sms;
+  if (scatter_ctas < 1) return false;
+  const double e = e_tile / scatter_ctas;
+  uint32_t cap = ((uint32_t)(e + 6.0 * std::sqrt(e) + 64.0) + 31u) & ~31u;
+  // SIEVE_BUCKET_CAP overrides the capacity (tests use a small one to make
+  // sub-buckets overflow and so exercise the tiles' fallback)
+  if (const char *env = std::getenv("SIEVE_BUCKET_CAP")) {
+    const long v = std::strtol(env, nullptr, 10);
+    if (v >= 1 && v < (long)cap) cap = (uint32_t)v;
+  }
+  BucketParams &b = plan->b;
+  memset(&b, 0, sizeof(b));
+  b.cap = cap;
+  b.ncta = (uint32_t)scatter_ctas;
+  b.i_large = i_large;
+  b.i_end = g.np;
+  b.k_begin = g.k_begin;
+  b.k_end = g.k_end;
+  b.L = g.L;
+  b.logW = log2u(g.L / 32);
+  b.primes = table.primes;
+  b.magic = table.magic;
+  b.cinv = table.cinv;
+  plan->wave = (uint32_t)ntl;
+  plan->sorted = sorted;
+  return true;
+}
+
+bool range_prefers_buckets(sieve_ctx *ctx, uint64_t lo, uint64_t hi) {
+  if (hi <= lo || hi > (1ull << 63) || isqrt_u64(hi - 1) > ctx->table.limit) return false;
+  RangeGeom g;
+  if (range_geometry(ctx, ctx->table, lo, hi, 0, false, &g) != SIEVE_OK) return false;
+  return plan_buckets(ctx, ctx->table, g, nullptr);
+}
+
+// Bucket buffers of the context (kept across calls, grown on demand).
+static int ensure_buckets(sieve_ctx *ctx, size_t bytes) {
+  if (bytes <= ctx->bucket_bytes) return SIEVE_OK;
+  if (ctx->d_bucket) {
+    SIEVE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->d_bucket);
+    ctx->d_bucket = nullptr;
+    ctx->bucket_bytes = 0;
+  }
+  SIEVE_CUDA_TRY(cudaMalloc(&ctx->d_bucket, bytes));
+  ctx->bucket_bytes = bytes;
+  return SIEVE_OK;
 }
 
 int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req, size_t *n_out) {
@@ -416,56 +649,14 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
     return SIEVE_ERR_RANGE;
   }
 
-  // tiles
-  const uint64_t k_begin = req.lo / 6;
-  const uint64_t k_end = (req.hi + 4) / 6;  // ceil((hi - 1) / 6)
-  const uint64_t span = k_end > k_begin ? k_end - k_begin : 0;
-  const int threads = (int)ctx->opt.block_threads;
-  uint32_t L = ctx->opt.tile_bits;
-  if (req.seg_width) {  // at most one segment boundary per tile: 6 L <= seg_width
-    const uint32_t lw = floor_pow2(req.seg_width / 6);
-    if (lw < L) L = lw;
-  }
-  size_t smem = (size_t)L / 4;
-  int per_sm = 0;
-  int rc = dispatch_occupancy(threads, &per_sm, req.list != 0, smem);
+  RangeGeom g;
+  int rc = range_geometry(ctx, table, req.lo, req.hi, req.seg_width, req.list != 0, &g);
   if (rc != SIEVE_OK) return rc;
-  if (per_sm < 1) {
-    set_error("tile of %u bits does not fit on an SM", L);
-    return SIEVE_ERR_INVALID;
-  }
-  if (ctx->opt.ctas_per_sm && (int)ctx->opt.ctas_per_sm < per_sm) per_sm = (int)ctx->opt.ctas_per_sm;
-  const uint64_t slots = (uint64_t)ctx->num_sms * (uint64_t)per_sm;
-  // small ranges: shrink tiles so that every CTA slot gets work
-  if (span > 0 && span < (uint64_t)L * slots) {
-    const uint64_t want = (span + slots - 1) / slots;
-    uint32_t lw = floor_pow2(want);
-    if (lw < want) lw *= 2;
-    if (lw < 1024) lw = 1024;
-    if (lw < L) L = lw;
-    smem = (size_t)L / 4;
-  }
-  const uint64_t ntiles64 = span ? (span + L - 1) / L : 0;
-  if (ntiles64 > 0xFFFFFFF0ull) {
-    set_error("range needs too many tiles");
-    return SIEVE_ERR_INVALID;
-  }
-  const uint32_t ntiles = (uint32_t)ntiles64;
-  const int grid = (int)std::min<uint64_t>(ntiles ? ntiles : 1, slots);
-
-  // primes needed and the warp/lane split: a warp takes a prime while it has
-  // >= group_hits hits per lane in a tile, i.e. P <= L / (32 * group_hits)
-  const uint32_t np = host_prime_count_le_table(table, s);
-  const uint64_t gmax = L / (32ull * std::max<uint32_t>(1u, ctx->opt.group_hits));
-  const uint32_t i_first = first_struck_prime_index((int)ctx->opt.presieve_groups);
-  uint32_t i_split = std::min(host_prime_count_le_table(table, gmax), np);
-  if (i_split < i_first) i_split = i_first;
-  smem += (size_t)(i_split - i_first) * sizeof(uint2);
-  if (smem > (size_t)ctx->smem_optin) {
-    set_error("tile of %u bits with %u warp-band primes needs %zu bytes of shared memory", L, i_split - i_first,
-              smem);
-    return SIEVE_ERR_INVALID;
-  }
+  const uint64_t k_begin = g.k_begin, k_end = g.k_end;
+  const int threads = g.threads;
+  const uint32_t L = g.L, ntiles = g.ntiles, np = g.np, i_first = g.i_first, i_split = g.i_split;
+  const int grid = g.grid;
+  size_t smem = g.smem;
 
   RangeKernelParams p;
   memset(&p, 0, sizeof(p));
@@ -538,8 +729,39 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
     phase_event(ctx, 0);
   }
   if (ntiles) {
-    rc = dispatch_launch(ctx, threads, p, req.list != 0, grid, smem);
-    if (rc != SIEVE_OK) return rc;
+    BucketPlan plan;
+    if (plan_buckets(ctx, table, g, &plan)) {
+      // the bucket sieve: per wave, the scatter, then the wave's tiles
+      BucketParams &bk = plan.b;
+      const uint32_t wave = plan.wave;
+      const size_t n_sub = (size_t)wave * bk.ncta;
+      const size_t off_counts = align_up(n_sub * bk.cap * sizeof(uint32_t), 256);
+      const size_t off_ovf = align_up(off_counts + n_sub * sizeof(uint32_t), 256);
+      rc = ensure_buckets(ctx, off_ovf + (size_t)wave * sizeof(uint32_t));
+      if (rc != SIEVE_OK) return rc;
+      char *bb = (char *)ctx->d_bucket;
+      bk.entries = (uint32_t *)bb;
+      bk.counts = (uint32_t *)(bb + off_counts);
+      bk.overflow = (uint32_t *)(bb + off_ovf);
+      SIEVE_CUDA_TRY(cudaMemsetAsync(bk.overflow, 0, (size_t)wave * sizeof(uint32_t), st));
+      const size_t ssmem = scatter_smem(plan.sorted, wave);
+      for (uint32_t t0 = 0; t0 < ntiles; t0 += wave) {
+        bk.t_begin = t0;
+        bk.ntl = std::min(wave, ntiles - t0);
+        if (plan.sorted)
+          bucket_scatter_kernel<kScatterBlock, kScatterHits><<<bk.ncta, kScatterBlock, ssmem, st>>>(bk);
+        else
+          bucket_scatter_direct_kernel<kScatterBlock><<<bk.ncta, kScatterBlock, ssmem, st>>>(bk);
+        ctx->launches++;
+        SIEVE_CUDA_TRY(cudaGetLastError());
+        rc = dispatch_launch(ctx, threads, p, req.list != 0, (int)std::min<uint32_t>(grid, bk.ntl), smem, &bk);
+        if (rc != SIEVE_OK) return rc;
+      }
+      if (ctx->phase_timing) ctx->ph.bucket_waves = (ntiles + wave - 1) / wave;
+    } else {
+      rc = dispatch_launch(ctx, threads, p, req.list != 0, grid, smem);
+      if (rc != SIEVE_OK) return rc;
+    }
   }
   phase_event(ctx, 1);
 

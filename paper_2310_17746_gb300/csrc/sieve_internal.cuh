@@ -304,6 +304,10 @@ struct sieve_ctx {
   // growable device staging for list output bound for host memory
   void *d_stage = nullptr;
   size_t stage_bytes = 0;
+  // bucket sieve buffers of single-range calls (entries, counts, overflow
+  // flags), kept across calls and grown on demand (range.cu)
+  void *d_bucket = nullptr;
+  size_t bucket_bytes = 0;
   // device address of the fixed scratch array of sieve_range_list_noalloc,
   // looked up by sieve_create with this context's device current (noalloc.cu)
   void *noalloc_scratch = nullptr;
@@ -376,5 +380,11 @@ struct RangeRequest {
 };
 
 int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req, size_t *n_out);
+
+// Whether run_range would send the large primes of a count of [lo, hi) through
+// the bucket sieve (range.cu); sieve_range then keeps the range on the tile
+// path instead of routing it to the batch path's strips (the buckets measured
+// faster on every far range tried).
+bool range_prefers_buckets(sieve_ctx *ctx, uint64_t lo, uint64_t hi);
 
 }  // namespace sieve

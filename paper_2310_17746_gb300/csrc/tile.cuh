@@ -167,14 +167,22 @@ __device__ __forceinline__ void warp_band_starts(uint2 *starts, uint64_t B, uint
 // constants only for primes below the tile span, so that larger ones keep a
 // one-remainder miss test, was slower: the load then waits for the prime.)
 template <int BLOCK>
+__device__ __forceinline__ void strike_lane_band(uint32_t *s1, uint32_t *s5, uint64_t B, const TileGeom &tg,
+                                                 const uint32_t *__restrict__ primes,
+                                                 const uint64_t *__restrict__ magic,
+                                                 const uint2 *__restrict__ cinv, uint32_t i_lo, uint32_t np,
+                                                 bool all_sq, uint64_t K0);
+
+template <int BLOCK>
 __device__ __forceinline__ void strike_primes(uint32_t *s1, uint32_t *s5, uint64_t B, const TileGeom &tg,
                                               const uint32_t *__restrict__ primes,
                                               const uint64_t *__restrict__ magic, const uint2 *__restrict__ cinv,
                                               const uint2 *starts, uint32_t i_first, uint32_t i_split, uint32_t np,
-                                              bool all_sq, uint32_t *next, uint64_t K0) {
+                                              bool all_sq, uint32_t *next, uint64_t K0,
+                                              uint32_t lane_end = 0xFFFFFFFFu) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t split = i_split < np ? i_split : np;
-  const uint32_t len = tg.len, wmask = tg.W - 1, logW = tg.logW, span6 = 6 * tg.len;
+  const uint32_t len = tg.len, wmask = tg.W - 1, logW = tg.logW;
   for (;;) {
     uint32_t i = 0;
     if (lane == 0) i = atomicAdd(next, 1u);
@@ -186,12 +194,31 @@ __device__ __forceinline__ void strike_primes(uint32_t *s1, uint32_t *s5, uint64
     if (k1 < len) strike(s1, k1, 32u * P, len, wmask, logW);
     if (k5 < len) strike(s5, k5, 32u * P, len, wmask, logW);
   }
+  // primes from the warp band's end up to np (or lane_end: above it the
+  // bucket sieve applies them) by one lane each
+  strike_lane_band<BLOCK>(s1, s5, B, tg, primes, magic, cinv, split > i_first ? split : i_first,
+                          np < lane_end ? np : lane_end, all_sq, K0);
+}
+
+// Strike the primes with table index in [i_lo, np) into the tile whose index
+// 0 is value B (K0 = B / 6), one lane per prime: each lane locates its prime's
+// first hits from the inverse-of-6 constants (the Table 1 start, see
+// starts_from_inverse) or, where the P^2 clamp can apply, with Table 1 itself
+// (all_sq: the caller knows that every prime below np has P^2 <= B and
+// P < 2^31, so the test per prime is skipped).
+template <int BLOCK>
+__device__ __forceinline__ void strike_lane_band(uint32_t *s1, uint32_t *s5, uint64_t B, const TileGeom &tg,
+                                                 const uint32_t *__restrict__ primes,
+                                                 const uint64_t *__restrict__ magic,
+                                                 const uint2 *__restrict__ cinv, uint32_t i_lo, uint32_t np,
+                                                 bool all_sq, uint64_t K0) {
+  const uint32_t len = tg.len, wmask = tg.W - 1, logW = tg.logW, span6 = 6 * tg.len;
   // one lane per prime; the next prime's table entries are loaded before the
   // current prime is struck so that their latency overlaps the strikes.  The
   // loop is unrolled by two with the prefetched entries alternating between
   // two register sets (fewer moves than rotating one set; measured).
   auto lane_loop = [&](auto &&one) {
-    uint32_t i = (split > i_first ? split : i_first) + threadIdx.x;
+    uint32_t i = i_lo + threadIdx.x;
     uint32_t P = 0;
     uint64_t m = 0;
     uint2 c = make_uint2(0, 0);
