@@ -105,7 +105,11 @@ typedef struct {
                               sorted scatter (a round's hits sorted by tile in shared memory,
                               written in runs), 0 = direct while a wave's entries fit in L2,
                               else sorted with waves of at least 4 tiles per CTA              */
-  uint32_t reserved[1];
+  uint32_t list_single_pass; /* single-range lists into device memory: 1 = one pass (each tile
+                              compacted from shared memory at an offset found by look-back over
+                              the tiles before it), 0 = two passes (bitmaps to global memory,
+                              scan, compaction; the default, measured faster); host-bound
+                              lists always take two passes                                    */
 } sieve_options;
 
 /* ---------------------------------------------------------------- context */

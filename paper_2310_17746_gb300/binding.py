@@ -53,14 +53,15 @@ class Options(ctypes.Structure):
                 ("presieve_groups", ctypes.c_uint32), ("batch_tile_bits", ctypes.c_uint32),
                 ("chunk_primes", ctypes.c_uint32), ("bucket_threshold", ctypes.c_uint32),
                 ("bucket_wave", ctypes.c_uint32), ("bucket_scatter", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 1)]
+                ("list_single_pass", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {"tile_bits": self.tile_bits, "block_threads": self.block_threads,
                 "ctas_per_sm": self.ctas_per_sm, "group_hits": self.group_hits,
                 "presieve_groups": self.presieve_groups, "batch_tile_bits": self.batch_tile_bits,
                 "chunk_primes": self.chunk_primes, "bucket_threshold": self.bucket_threshold,
-                "bucket_wave": self.bucket_wave, "bucket_scatter": self.bucket_scatter}
+                "bucket_wave": self.bucket_wave, "bucket_scatter": self.bucket_scatter,
+                "list_single_pass": self.list_single_pass}
 
 
 class ServerConfig(ctypes.Structure):

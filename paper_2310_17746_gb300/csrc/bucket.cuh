@@ -46,6 +46,7 @@ struct BucketParams {
   uint32_t i_end;
   uint32_t t_begin;     // first tile of the wave (tile index within the range)
   uint32_t ntl;         // tiles in the wave
+  uint32_t wave_id;     // index of the wave in the call
   // range geometry and base table (as the tile kernel sees them)
   uint64_t k_begin, k_end;
   uint32_t L, logW;

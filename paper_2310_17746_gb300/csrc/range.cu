@@ -13,6 +13,8 @@
 #include <cstdlib>
 #include <cstring>
 
+#include <cuda/atomic>
+
 #include "bucket.cuh"
 #include "tile.cuh"
 
@@ -40,18 +42,108 @@ struct RangeKernelParams {
   uint64_t seg_width;       // 0: no per-segment counts
   uint64_t first_seg;       // floor(lo / seg_width)
   unsigned long long *bins;
-  // list mode
+  // list mode with bitmap write-out (kModeListBitmap)
   uint32_t *tile_counts;    // per tile
   uint2 *bitmap;            // per tile L/32 (class-1 word, class-5 word) pairs
+  // single-pass list mode (kModeListFused)
+  unsigned long long *tile_state;  // per tile: look-back word (flag << 62 | count), zeroed per call
+  uint32_t *tile_counter;          // per launch (bucket wave): next tile to take, zeroed per call
+  unsigned long long *error;       // set to 1 when a look-back gave up (the call reports TIMEOUT)
+  void *out;                       // device output, uint32 or uint64 per out_bytes
+  uint64_t cap;                    // elements of out; positions >= cap are not written
+  uint32_t out_bytes;
+  uint32_t stage_off;              // words from the start of dynamic shared memory to the staging
 };
+
+// What the tile kernel produces: counts only; counts plus each tile's bitmap
+// in global memory (for scan_tile_counts_kernel and compact_kernel); or
+// counts plus the list itself, each tile compacted straight from shared
+// memory at an offset found by decoupled look-back (one pass).
+constexpr int kModeCount = 0;
+constexpr int kModeListBitmap = 1;
+constexpr int kModeListFused = 2;
+
+// Decoupled look-back (Merrill & Garland, "Single-pass Parallel Prefix Scan
+// with Decoupled Look-back", 2016) over per-tile words flag << 62 | value:
+// flag 1 = the tile's own count is known, 2 = its inclusive prefix is known,
+// 3 = a look-back before it failed.  Tiles are taken from an atomic counter,
+// so every tile before the current one is held by a running CTA that
+// publishes without waiting on later tiles; each poll that finds no flag
+// counts against kLookbackPolls (about a second of polling), after which the
+// tile publishes flag 3, as do all tiles after it, and the call fails.
+constexpr uint64_t kLookbackFlagShift = 62;
+constexpr uint64_t kLookbackValueMask = (1ull << kLookbackFlagShift) - 1;
+constexpr uint32_t kLookbackPolls = 1u << 23;
+
+__device__ __forceinline__ void lookback_publish(unsigned long long *w, uint64_t flag, uint64_t value) {
+  cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> a(*w);
+  a.store((flag << kLookbackFlagShift) | (value & kLookbackValueMask), cuda::memory_order_release);
+}
+
+// Exclusive prefix of tile t's count, by warp 0 (every lane returns it); false
+// if it failed.  Each step reads the 32 words before the window's end at once
+// (lane l: tile j - l), and stops at the nearest one carrying an inclusive
+// prefix: the prefix is that value plus the counts of the tiles after it.
+// When one of the 32 still has no flag, the warp polls the same window again.
+__device__ __forceinline__ bool lookback_prefix_warp(unsigned long long *state, uint32_t t, uint64_t cnt,
+                                                     uint64_t *excl) {
+  const uint32_t lane = threadIdx.x & 31;
+  if (t == 0) {
+    if (lane == 0) lookback_publish(state, 2, cnt);
+    *excl = 0;
+    return true;
+  }
+  if (lane == 0) lookback_publish(state + t, 1, cnt);
+  uint64_t sum = 0;
+  uint32_t polls = 0;
+  bool ok = true;
+  int64_t j = (int64_t)t - 1;  // the window is tiles j - 31 .. j
+  while (j >= 0) {
+    const int64_t mine = j - (int64_t)lane;
+    uint64_t w = (2ull << kLookbackFlagShift);  // below tile 0: an inclusive prefix of 0
+    if (mine >= 0) {
+      cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> a(state[mine]);
+      w = a.load(cuda::memory_order_acquire);
+    }
+    const uint32_t f = (uint32_t)(w >> kLookbackFlagShift);
+    const uint32_t has_p = __ballot_sync(kFullMask, f == 2), bad = __ballot_sync(kFullMask, f == 3);
+    const uint32_t empty = __ballot_sync(kFullMask, f == 0);
+    // lanes up to the nearest inclusive prefix (the lowest lane with f == 2)
+    const uint32_t stop = has_p ? (uint32_t)(__ffs(has_p) - 1) : 31u;
+    const uint32_t upto = stop == 31 ? 0xFFFFFFFFu : ((2u << stop) - 1u);
+    if (bad & upto) {
+      ok = false;
+      break;
+    }
+    if (empty & upto) {  // a tile in the window has not published its count yet
+      if (++polls > kLookbackPolls) {
+        ok = false;
+        break;
+      }
+      __nanosleep(100);
+      continue;
+    }
+    uint64_t v = lane <= stop ? (w & kLookbackValueMask) : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFullMask, v, o);
+    sum += __shfl_sync(kFullMask, v, 0);
+    if (has_p) break;
+    j -= 32;
+  }
+  if (lane == 0) lookback_publish(state + t, ok ? 2 : 3, sum + cnt);
+  *excl = sum;
+  return ok;
+}
 
 // BUCKET: the launch sieves the tiles of one bucket wave, [b.t_begin,
 // b.t_begin + b.ntl); the primes with table index >= b.i_large are applied by
 // draining the wave's buckets (bucket.cuh) instead of being located in every
 // tile.  Without BUCKET the launch sieves every tile and b is unused.
-template <int BLOCK, bool LIST, bool BUCKET>
+template <int BLOCK, int MODE, bool BUCKET>
 __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const RangeKernelParams p,
                                                                           const BucketParams b) {
+  constexpr bool LIST = MODE == kModeListBitmap;
+  constexpr bool FUSED = MODE == kModeListFused;
   constexpr int NWARPS = BLOCK / 32;
   extern __shared__ uint32_t smem[];
   const uint32_t W = p.L / 32;
@@ -64,18 +156,30 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
   __shared__ int64_t sh_t1, sh_t5;
   __shared__ int sh_has_boundary;
   __shared__ uint32_t sh_overflow;
+  __shared__ uint32_t sh_tile;                // FUSED: the tile taken next
+  __shared__ uint64_t sh_excl;                // FUSED: the tile's output offset
+  __shared__ int sh_lb_ok;
   __shared__ uint64_t red[3 * NWARPS];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t t_begin = BUCKET ? b.t_begin : 0u;
   const uint32_t t_end = BUCKET ? b.t_begin + b.ntl : p.ntiles;
+  uint32_t *const counter = FUSED ? p.tile_counter + (BUCKET ? b.wave_id : 0u) : nullptr;
   uint32_t np_prev = 0;  // warp 0: the previous tile's prime count
+  // tiles in grid-stride order, or (FUSED) from the counter, in increasing
+  // order over the CTAs, as the look-back needs
+  uint32_t t = t_begin + blockIdx.x;
+  if (FUSED) {
+    if (threadIdx.x == 0) sh_tile = t_begin + atomicAdd(counter, 1u);
+    __syncthreads();
+    t = sh_tile;
+  }
   // the pattern offsets K0 mod period: computed once per tile by a few
   // threads (for the next tile at the end of this one), not by every thread
-  if (threadIdx.x < (uint32_t)p.npat && t_begin + blockIdx.x < t_end)
-    sh_poff[threadIdx.x] = pattern_offset(p.k_begin + (uint64_t)(t_begin + blockIdx.x) * p.L, p.pd[threadIdx.x]);
+  if (threadIdx.x < (uint32_t)p.npat && t < t_end)
+    sh_poff[threadIdx.x] = pattern_offset(p.k_begin + (uint64_t)t * p.L, p.pd[threadIdx.x]);
   __syncthreads();
 
-  for (uint32_t t = t_begin + blockIdx.x; t < t_end; t += gridDim.x) {
+  while (t < t_end) {
     const uint64_t K0 = p.k_begin + (uint64_t)t * p.L;
     const uint64_t left = p.k_end - K0;
     TileGeom tg;
@@ -194,6 +298,7 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
     }
     uint64_t cnt = (uint64_t)wc1 + wc5, below = wbl;
     uint64_t sum = (uint64_t)wc1 * (6 * K0 + 1) + (uint64_t)wc5 * (6 * K0 + 5) + 6ull * wsw + 6ull * W * wbs;
+    if (FUSED && threadIdx.x == 0) sh_tile = t_begin + atomicAdd(counter, 1u);  // read after the next barrier
     block_sum3_warps<BLOCK>(cnt, sum, below, red);
     if (threadIdx.x == 0) {
       if (K0 == 0) {  // 2 and 3 are outside the residue arrays (Section 2.1)
@@ -216,10 +321,51 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
         }
       }
     }
-    const uint32_t tn = t + gridDim.x;  // the next tile's pattern offsets (a warp other than thread 0's)
+    if (FUSED) {
+      // the tile's output offset, then its survivors straight from shared memory
+      if (warp == 0) {
+        const uint64_t c = __shfl_sync(kFullMask, cnt, 0);  // thread 0 holds the tile's count
+        uint64_t excl = 0;
+        const bool ok = lookback_prefix_warp(p.tile_state, t, c, &excl);
+        if (lane == 0) {
+          sh_lb_ok = ok;
+          if (!ok) atomicExch(p.error, 1ull);
+          sh_excl = excl;
+        }
+      }
+      __syncthreads();
+      if (sh_lb_ok) {
+        uint64_t off = sh_excl;
+        uint32_t *stage_w = smem + p.stage_off;
+        uint32_t *warp_cnt = stage_w + fused_stage_bytes(BLOCK) / sizeof(uint32_t);
+        if (K0 == 0 && threadIdx.x == 0) {  // 2 and 3 first
+          uint64_t o = off;
+          const bool e2 = p.lo <= 2 && 2 < p.hi, e3 = p.lo <= 3 && 3 < p.hi;
+          if (p.out_bytes == 4) {
+            if (e2 && o < p.cap) ((uint32_t *)p.out)[o] = 2;
+            o += e2;
+            if (e3 && o < p.cap) ((uint32_t *)p.out)[o] = 3;
+          } else {
+            if (e2 && o < p.cap) ((uint64_t *)p.out)[o] = 2;
+            o += e2;
+            if (e3 && o < p.cap) ((uint64_t *)p.out)[o] = 3;
+          }
+        }
+        if (K0 == 0) off += (p.lo <= 2 && 2 < p.hi) + (p.lo <= 3 && 3 < p.hi);
+        if (p.out_bytes == 4)
+          compact_tile_smem<BLOCK, uint32_t>(s1, s5, tg.logW, K0, off, (uint32_t *)p.out, p.cap, warp_cnt,
+                                             (uint8_t *)stage_w);
+        else
+          compact_tile_smem<BLOCK, uint64_t>(s1, s5, tg.logW, K0, off, (uint64_t *)p.out, p.cap, warp_cnt,
+                                             (uint8_t *)stage_w);
+      }
+    }
+    // the next tile and its pattern offsets (a warp other than thread 0's)
+    const uint32_t tn = FUSED ? sh_tile : t + gridDim.x;
     if (threadIdx.x >= 32 && threadIdx.x < 32 + (uint32_t)p.npat && tn < t_end)
       sh_poff[threadIdx.x - 32] = pattern_offset(p.k_begin + (uint64_t)tn * p.L, p.pd[threadIdx.x - 32]);
     __syncthreads();
+    t = tn;
   }
 }
 
@@ -318,21 +464,30 @@ static size_t compact_smem_bytes(uint32_t L) {
 
 namespace {
 
-template <int BLOCK>
-int launch_range_tiles(sieve_ctx *ctx, const RangeKernelParams &p, const BucketParams *b, bool list, int grid,
-                       size_t smem) {
-  BucketParams none;
-  memset(&none, 0, sizeof(none));
+template <int BLOCK, int MODE>
+void launch_mode(sieve_ctx *ctx, const RangeKernelParams &p, const BucketParams *b, int grid, size_t smem) {
   if (b) {
-    if (list)
-      range_tiles_kernel<BLOCK, true, true><<<grid, BLOCK, smem, ctx->stream>>>(p, *b);
-    else
-      range_tiles_kernel<BLOCK, false, true><<<grid, BLOCK, smem, ctx->stream>>>(p, *b);
+    range_tiles_kernel<BLOCK, MODE, true><<<grid, BLOCK, smem, ctx->stream>>>(p, *b);
   } else {
-    if (list)
-      range_tiles_kernel<BLOCK, true, false><<<grid, BLOCK, smem, ctx->stream>>>(p, none);
-    else
-      range_tiles_kernel<BLOCK, false, false><<<grid, BLOCK, smem, ctx->stream>>>(p, none);
+    BucketParams none;
+    memset(&none, 0, sizeof(none));
+    range_tiles_kernel<BLOCK, MODE, false><<<grid, BLOCK, smem, ctx->stream>>>(p, none);
+  }
+}
+
+template <int BLOCK>
+int launch_range_tiles(sieve_ctx *ctx, const RangeKernelParams &p, const BucketParams *b, int mode, int grid,
+                       size_t smem) {
+  if (mode == kModeListFused) {
+    if (BLOCK == 256) {
+      set_error("the single-pass list kernel needs 512 or 1024 threads");
+      return SIEVE_ERR_INVALID;
+    }
+    launch_mode<BLOCK, kModeListFused>(ctx, p, b, grid, smem);
+  } else if (mode == kModeListBitmap) {
+    launch_mode<BLOCK, kModeListBitmap>(ctx, p, b, grid, smem);
+  } else {
+    launch_mode<BLOCK, kModeCount>(ctx, p, b, grid, smem);
   }
   ctx->launches++;
   SIEVE_CUDA_TRY(cudaGetLastError());
@@ -342,23 +497,28 @@ int launch_range_tiles(sieve_ctx *ctx, const RangeKernelParams &p, const BucketP
 template <int BLOCK>
 int occupancy(int *blocks, bool list, size_t smem) {
   cudaError_t e = list ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                             blocks, range_tiles_kernel<BLOCK, true, false>, BLOCK, smem)
+                             blocks, range_tiles_kernel<BLOCK, kModeListBitmap, false>, BLOCK, smem)
                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                             blocks, range_tiles_kernel<BLOCK, false, false>, BLOCK, smem);
+                             blocks, range_tiles_kernel<BLOCK, kModeCount, false>, BLOCK, smem);
   SIEVE_CUDA_TRY(e);
+  return SIEVE_OK;
+}
+
+template <int BLOCK, int MODE>
+int set_smem_attr_mode(int bytes) {
+  SIEVE_CUDA_TRY(cudaFuncSetAttribute(range_tiles_kernel<BLOCK, MODE, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  SIEVE_CUDA_TRY(cudaFuncSetAttribute(range_tiles_kernel<BLOCK, MODE, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   return SIEVE_OK;
 }
 
 template <int BLOCK>
 int set_smem_attr(int bytes) {
-  SIEVE_CUDA_TRY(cudaFuncSetAttribute(range_tiles_kernel<BLOCK, true, false>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  SIEVE_CUDA_TRY(cudaFuncSetAttribute(range_tiles_kernel<BLOCK, false, false>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  SIEVE_CUDA_TRY(cudaFuncSetAttribute(range_tiles_kernel<BLOCK, true, true>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  SIEVE_CUDA_TRY(cudaFuncSetAttribute(range_tiles_kernel<BLOCK, false, true>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  int rc;
+  if ((rc = set_smem_attr_mode<BLOCK, kModeCount>(bytes)) != SIEVE_OK) return rc;
+  if ((rc = set_smem_attr_mode<BLOCK, kModeListBitmap>(bytes)) != SIEVE_OK) return rc;
+  if (BLOCK != 256) return set_smem_attr_mode<BLOCK, kModeListFused>(bytes);
   return SIEVE_OK;
 }
 
@@ -370,12 +530,12 @@ int dispatch_occupancy(int threads, int *blocks, bool list, size_t smem) {
   }
 }
 
-int dispatch_launch(sieve_ctx *ctx, int threads, const RangeKernelParams &p, bool list, int grid, size_t smem,
+int dispatch_launch(sieve_ctx *ctx, int threads, const RangeKernelParams &p, int mode, int grid, size_t smem,
                     const BucketParams *b = nullptr) {
   switch (threads) {
-    case 256: return launch_range_tiles<256>(ctx, p, b, list, grid, smem);
-    case 512: return launch_range_tiles<512>(ctx, p, b, list, grid, smem);
-    default: return launch_range_tiles<1024>(ctx, p, b, list, grid, smem);
+    case 256: return launch_range_tiles<256>(ctx, p, b, mode, grid, smem);
+    case 512: return launch_range_tiles<512>(ctx, p, b, mode, grid, smem);
+    default: return launch_range_tiles<1024>(ctx, p, b, mode, grid, smem);
   }
 }
 
@@ -692,14 +852,35 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
     SIEVE_CUDA_TRY(cudaMemsetAsync(acc, 0, 2 * sizeof(unsigned long long), st));
   }
 
-  // scratch layout: [bins (host-output case)] [tile counts] [offsets] [bitmap] [list staging]
+  BucketPlan plan;
+  const bool use_buckets = ntiles && plan_buckets(ctx, table, g, &plan);
+  const uint32_t nwaves = use_buckets ? (ntiles + plan.wave - 1) / plan.wave : 1;
+  // single-pass list: device output, 512 or 1024 threads, and room in shared
+  // memory for the emission staging (it reuses the warp-band starts' space)
+  const int nwarps = threads / 32;
+  const size_t fused_smem =
+      (size_t)L / 4 + std::max(align_up((size_t)(i_split - i_first) * sizeof(uint2), 16),
+                               fused_stage_bytes(threads) + (size_t)nwarps * 32 * sizeof(uint32_t));
+  const bool fused = req.list && dev_out && threads != 256 && ctx->opt.list_single_pass &&
+                     fused_smem <= (size_t)ctx->smem_optin;
+
+  // scratch layout: [bins (host-output case)] [tile counts] [offsets] [bitmap]
+  // (two-pass list) or [tile states] [tile counters] [error word] (single pass)
   size_t off_bins = 0, off_counts = 0, off_offsets = 0, off_bitmap = 0, need = 0;
+  size_t off_state = 0, off_ctr = 0, off_err = 0;
   const bool bins_direct = dev_out;
   if (req.seg_width && !bins_direct) {
     off_bins = need;
     need = align_up(need + req.nbins * sizeof(uint64_t), 256);
   }
-  if (req.list) {
+  if (fused) {
+    off_state = need;
+    need = align_up(need + (size_t)ntiles * sizeof(uint64_t), 256);
+    off_ctr = need;
+    need = align_up(need + (size_t)nwaves * sizeof(uint32_t), 256);
+    off_err = need;
+    need = align_up(need + sizeof(uint64_t), 256);
+  } else if (req.list) {
     off_counts = need;
     need = align_up(need + (size_t)ntiles * sizeof(uint32_t), 256);
     off_offsets = need;
@@ -716,10 +897,21 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
     p.bins = bins_direct ? (unsigned long long *)req.bins : (unsigned long long *)(scr + off_bins);
     SIEVE_CUDA_TRY(cudaMemsetAsync(p.bins, 0, req.nbins * sizeof(uint64_t), st));
   }
-  if (req.list) {
+  if (fused) {
+    p.tile_state = (unsigned long long *)(scr + off_state);
+    p.tile_counter = (uint32_t *)(scr + off_ctr);
+    p.error = (unsigned long long *)(scr + off_err);
+    SIEVE_CUDA_TRY(cudaMemsetAsync(scr + off_state, 0, off_err + sizeof(uint64_t) - off_state, st));
+    p.out = req.out;
+    p.cap = req.cap;
+    p.out_bytes = (uint32_t)req.out_bytes;
+    p.stage_off = 2 * (L / 32);
+    smem = fused_smem;
+  } else if (req.list) {
     p.tile_counts = (uint32_t *)(scr + off_counts);
     p.bitmap = (uint2 *)(scr + off_bitmap);
   }
+  const int mode = fused ? kModeListFused : (req.list ? kModeListBitmap : kModeCount);
 
   if (ctx->phase_timing) {
     ctx->ph = sieve_phase_times{};
@@ -729,8 +921,7 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
     phase_event(ctx, 0);
   }
   if (ntiles) {
-    BucketPlan plan;
-    if (plan_buckets(ctx, table, g, &plan)) {
+    if (use_buckets) {
       // the bucket sieve: per wave, the scatter, then the wave's tiles
       BucketParams &bk = plan.b;
       const uint32_t wave = plan.wave;
@@ -748,22 +939,51 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
       for (uint32_t t0 = 0; t0 < ntiles; t0 += wave) {
         bk.t_begin = t0;
         bk.ntl = std::min(wave, ntiles - t0);
+        bk.wave_id = t0 / wave;
         if (plan.sorted)
           bucket_scatter_kernel<kScatterBlock, kScatterHits><<<bk.ncta, kScatterBlock, ssmem, st>>>(bk);
         else
           bucket_scatter_direct_kernel<kScatterBlock><<<bk.ncta, kScatterBlock, ssmem, st>>>(bk);
         ctx->launches++;
         SIEVE_CUDA_TRY(cudaGetLastError());
-        rc = dispatch_launch(ctx, threads, p, req.list != 0, (int)std::min<uint32_t>(grid, bk.ntl), smem, &bk);
+        rc = dispatch_launch(ctx, threads, p, mode, (int)std::min<uint32_t>(grid, bk.ntl), smem, &bk);
         if (rc != SIEVE_OK) return rc;
       }
       if (ctx->phase_timing) ctx->ph.bucket_waves = (ntiles + wave - 1) / wave;
     } else {
-      rc = dispatch_launch(ctx, threads, p, req.list != 0, grid, smem);
+      rc = dispatch_launch(ctx, threads, p, mode, grid, smem);
       if (rc != SIEVE_OK) return rc;
     }
   }
   phase_event(ctx, 1);
+
+  if (fused) {  // the list is written: read the total (the last tile's inclusive prefix) and the error word
+    ctx->h_acc[2] = 0;
+    ctx->h_acc[3] = 0;
+    if (ntiles) {
+      SIEVE_CUDA_TRY(cudaMemcpyAsync(ctx->h_acc + 2, p.tile_state + (ntiles - 1), sizeof(uint64_t),
+                                     cudaMemcpyDeviceToHost, st));
+      SIEVE_CUDA_TRY(cudaMemcpyAsync(ctx->h_acc + 3, p.error, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    }
+    SIEVE_CUDA_TRY(cudaMemcpyAsync(ctx->h_acc, acc, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    SIEVE_CUDA_TRY(cudaStreamSynchronize(st));
+    if (ctx->h_acc[3] || (ntiles && (ctx->h_acc[2] >> kLookbackFlagShift) != 2)) {
+      set_error("single-pass list: a tile's look-back gave up waiting for an earlier tile");
+      return SIEVE_ERR_TIMEOUT;
+    }
+    const uint64_t total = ctx->h_acc[2] & kLookbackValueMask;
+    if (n_out) *n_out = (size_t)total;
+    if (ctx->phase_timing) ctx->ph.listed = total < req.cap ? total : req.cap;
+    if (req.total) {
+      sieve_count_result r{ctx->h_acc[0], ctx->h_acc[1]};
+      SIEVE_CUDA_TRY(cudaMemcpy(req.total, &r, sizeof(r), cudaMemcpyHostToDevice));
+    }
+    if (total > req.cap) {
+      set_error("output capacity %zu is below the %llu primes found", req.cap, (unsigned long long)total);
+      return SIEVE_ERR_CAPACITY;
+    }
+    return SIEVE_OK;
+  }
 
   if (!req.list) {
     if (!dev_out) {
@@ -980,7 +1200,7 @@ int run_range_list_into(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t *out,
   uint64_t *offsets = (uint64_t *)(scr + off_offsets);
   SIEVE_CUDA_TRY(cudaMemsetAsync(ctx->d_acc, 0, 2 * sizeof(unsigned long long), st));
   if (ntiles) {
-    rc = dispatch_launch(ctx, threads, p, true, grid, smem);
+    rc = dispatch_launch(ctx, threads, p, kModeListBitmap, grid, smem);
     if (rc != SIEVE_OK) return rc;
     scan_tile_counts_kernel<1024><<<1, 1024, 0, st>>>(p.tile_counts, offsets, ntiles);
     ctx->launches++;

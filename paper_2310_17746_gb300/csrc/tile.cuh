@@ -590,4 +590,90 @@ __device__ __forceinline__ void compact_tile(const uint2 *__restrict__ bm, uint3
   flush();
 }
 
+// Staging bytes of compact_tile_smem for BLOCK threads: per warp 32 rows of
+// kFusedRow one-byte codes, rows kFusedPitch bytes apart (17 words: the 32
+// lanes' rows start in 32 different banks).
+constexpr uint32_t kFusedRow = 64;
+constexpr uint32_t kFusedPitch = 68;
+__host__ __device__ constexpr size_t fused_stage_bytes(int block) {
+  return (size_t)(block / 32) * 32 * kFusedPitch;
+}
+
+// compact_tile for a tile whose bitmaps are still in shared memory (s1, s5:
+// W words each, sliced layout): writes its survivors, in value order, to
+// out[off, ...), skipping every position >= cap.  Same two passes as
+// compact_tile (warp transposes give lane b row b's candidates of a 32-word
+// chunk; pass 1 counts per warp and row, a row-major prefix gives the
+// positions), but the staging codes are one byte, (chunk - c0) << 6 | j << 1
+// | class, so a warp flushes after at most four chunks or when a row would
+// overflow kFusedRow codes.  Bits outside the range must already be clear.
+template <int BLOCK, typename OutT>
+__device__ __forceinline__ void compact_tile_smem(const uint32_t *s1, const uint32_t *s5, uint32_t logW, uint64_t K0,
+                                                  uint64_t off, OutT *out, uint64_t cap, uint32_t *warp_cnt,
+                                                  uint8_t *stage) {
+  constexpr int NWARPS = BLOCK / 32;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t W = 1u << logW, C = W / 32;
+  const uint32_t c_begin = (uint32_t)((uint64_t)warp * C / NWARPS);
+  const uint32_t c_end = (uint32_t)((uint64_t)(warp + 1) * C / NWARPS);
+  uint32_t cnt = 0;
+  for (uint32_t c = c_begin; c < c_end; c++)
+    cnt += __popc(warp_transpose32(s1[(c << 5) + lane], lane)) + __popc(warp_transpose32(s5[(c << 5) + lane], lane));
+  warp_cnt[warp * 32 + lane] = cnt;
+  __syncthreads();
+  if (warp == 0) {  // row-major prefix: rows in order, within a row the warps in order
+    uint32_t row = 0;
+    for (int g = 0; g < NWARPS; g++) row += warp_cnt[g * 32 + lane];
+    uint32_t incl = row;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFullMask, incl, o);
+      if (lane >= (uint32_t)o) incl += y;
+    }
+    uint32_t run = incl - row;
+    for (int g = 0; g < NWARPS; g++) {
+      const uint32_t cg = warp_cnt[g * 32 + lane];
+      warp_cnt[g * 32 + lane] = run;
+      run += cg;
+    }
+  }
+  __syncthreads();
+  uint32_t pos = warp_cnt[warp * 32 + lane];
+  uint8_t *const wst = stage + (size_t)warp * 32 * kFusedPitch;
+  uint8_t *const row = wst + lane * kFusedPitch;
+  const uint64_t v0 = 6 * K0;
+  uint32_t n = 0, c0 = c_begin;
+  auto flush = [&]() {
+    __syncwarp();
+    for (uint32_t r = 0; r < 32; r++) {
+      const uint32_t nr = __shfl_sync(kFullMask, n, r), pr = __shfl_sync(kFullMask, pos, r);
+      const uint8_t *rs = wst + r * kFusedPitch;
+      const uint64_t vr = v0 + 6ull * (((uint64_t)r << logW) + ((uint64_t)c0 << 5));
+      for (uint32_t i = lane; i < nr; i += 32) {
+        const uint32_t code = rs[i];
+        const uint64_t o = off + pr + i;
+        if (o < cap) out[o] = (OutT)(vr + 6ull * (code >> 1) + 1 + 4 * (code & 1));
+      }
+    }
+    __syncwarp();
+    pos += n;
+    n = 0;
+  };
+  for (uint32_t c = c_begin; c < c_end; c++) {
+    const uint32_t t1 = warp_transpose32(s1[(c << 5) + lane], lane), t5 = warp_transpose32(s5[(c << 5) + lane], lane);
+    const uint32_t rn = __popc(t1) + __popc(t5);
+    if (__any_sync(kFullMask, n + rn > kFusedRow) || c - c0 >= 4) {  // codes hold c - c0 < 4
+      flush();
+      c0 = c;
+    }
+    uint64_t m = spread_bits(t1) | (spread_bits(t5) << 1);
+    const uint32_t cb = (c - c0) << 6;
+    while (m) {
+      row[n++] = (uint8_t)(cb + (uint32_t)(__ffsll((long long)m) - 1));
+      m &= m - 1;
+    }
+  }
+  flush();
+}
+
 }  // namespace sieve

@@ -189,10 +189,17 @@ def test_phase_timing(sv):
         assert t["sieve_ms"] > 0 and t["scan_ms"] == 0 and t["compact_ms"] == 0 and t["listed"] == 0
         assert t["tiles"] * t["tile_len"] >= (hi - lo) // 6
         out = torch.zeros(want.count, dtype=torch.int64, device="cuda")
-        n = sv.range_list(lo, hi, out=out)
+        n = sv.range_list(lo, hi, out=out)  # two passes (default): tile kernel, scan, compaction
         t = sv.phase_times()
         assert n == want.count == t["listed"]
         assert t["sieve_ms"] > 0 and t["scan_ms"] > 0 and t["compact_ms"] > 0
+        np.testing.assert_array_equal(out.cpu().numpy().astype(np.uint64), oracle.list_range(lo, hi))
+        sv.set_options(list_single_pass=1)  # one pass: the tile kernel writes the list
+        out.zero_()
+        n = sv.range_list(lo, hi, out=out)
+        t = sv.phase_times()
+        assert n == want.count == t["listed"]
+        assert t["sieve_ms"] > 0 and t["scan_ms"] == 0 and t["compact_ms"] == 0
         np.testing.assert_array_equal(out.cpu().numpy().astype(np.uint64), oracle.list_range(lo, hi))
         sv.set_phase_timing(False)
         with pytest.raises(binding.SieveError):
