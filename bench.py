@@ -35,6 +35,8 @@ UNIT = "numbers/s"
 WIDTH = 10**12
 SEG_WIDTH = 1 << 30
 PI_1E12 = 37607912018  # published value (OEIS A006880), checked on every run
+TUNE_CACHE = os.path.join(ROOT, "paper_2310_17746_gb300", "tuned_options.json")
+TUNE_WORKLOAD = "count 1e12-wide range, 2^30-number blocks"
 
 
 def parse_args():
@@ -47,6 +49,8 @@ def parse_args():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-queries leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-list", action="store_true", help="skip the list leg")
+    ap.add_argument("--no-naive", action="store_true", help="skip the plain GPU sieve comparison")
+    ap.add_argument("--no-far", action="store_true", help="skip the far-range (bucket sieve) leg")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
@@ -259,6 +263,125 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- batch and serving legs
 
+def expected_strikes(lo, hi, first: int, primes) -> float:
+    """Expected strikes of a 6k+-1 sieve over the queries [lo[i], hi[i]) with
+    the primes below `first` presieved: a prime p strikes the class-1 and
+    class-5 multiples m >= max(lo, p^2) below hi, one in 3p of the numbers.
+    Primes up to sqrt(lo) give w / (3p); those in (sqrt(lo), sqrt(hi)] give
+    (hi - p^2) / (3p) = hi / (3p) - p / 3.  Summed with prefix sums of 1/p and
+    p over the primes, so that thousands of queries cost a few array passes
+    (an expected value: the exact count differs by rounding, < 1 per prime)."""
+    import numpy as np
+    p = primes[primes >= first].astype(np.float64)
+    inv = np.concatenate([[0.0], np.cumsum(1.0 / p)])
+    sp = np.concatenate([[0.0], np.cumsum(p)])
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    a = np.searchsorted(p, np.sqrt(lo), side="right")
+    b = np.searchsorted(p, np.sqrt(np.maximum(hi - 1, 0)), side="right")
+    w = hi - lo
+    low = w / 3.0 * inv[a]
+    high = hi / 3.0 * (inv[b] - inv[a]) - (sp[b] - sp[a]) / 3.0
+    return float(np.sum(low + np.maximum(high, 0.0)))
+
+
+def naive_leg() -> dict:
+    """The plain one-range-per-launch GPU sieve (sieve_range_naive: one bit
+    per odd number in global memory, a global atomic AND per multiple, then a
+    popcount pass) against the segmented path on the same GPU, for the three
+    range workloads: [2, 1e8] as a list, [2, 1e10] and [2, 1e12] as counts.
+    Device outputs, CUDA events on the context's stream; the naive call
+    allocates its bitmap (62.5 GB at 1e12) inside every call, by design."""
+    import numpy as np
+    import torch
+
+    from paper_2310_17746_gb300 import binding
+
+    st = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(st)
+            fn()
+            b.record(st)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return min(ts)
+
+    rows = []
+    for name, lo, hi, mode, reps in (("[2, 1e8] uint64 list", 2, 10**8 + 1, "list", 3),
+                                     ("[2, 1e10] count", 2, 10**10 + 1, "count", 2),
+                                     ("[2, 1e12] count", 2, 10**12 + 1, "count", 1)):
+        with binding.Sieve(hi) as sv:
+            if mode == "list":
+                n = sv.range_count(lo, hi).count
+                o1 = torch.empty(n, dtype=torch.int64, device="cuda")
+                o2 = torch.empty(n, dtype=torch.int64, device="cuda")
+                sv.range_list(lo, hi, out=o1)
+                sv.naive_list(lo, hi, out=o2)
+                assert torch.equal(o1, o2)
+                t_seg = timed(lambda: sv.range_list(lo, hi, out=o1), reps)
+                t_naive = timed(lambda: sv.naive_list(lo, hi, out=o2), reps)
+            else:
+                tot = torch.zeros(2, dtype=torch.int64, device="cuda")
+                sv.range_count(lo, hi, out=tot)
+                ref = sv.naive_count(lo, hi)
+                assert (int(tot[0]), int(tot[1]) % 2**64) == (ref.count, ref.checksum)
+                t_seg = timed(lambda: sv.range_count(lo, hi, out=tot, asynchronous=True), 3)
+                t_naive = timed(lambda: sv.naive_count(lo, hi), reps)
+        rows.append({"workload": name, "naive_ms": round(t_naive, 3), "segmented_ms": round(t_seg, 3),
+                     "speedup": round(t_naive / t_seg, 1), "naive_numbers_per_s": (hi - lo) / (t_naive / 1e3)})
+    return {"comparator": "sieve_range_naive (plain global-bitmap GPU sieve, one range per call)", "configs": rows}
+
+
+def far_leg(steps: int) -> dict:
+    """Far ranges through sieve_range (count, device output): the default
+    path (large primes through the bucket sieve) against the same call with
+    the bucket sieve off (every prime located in every tile, or, where the
+    planner prefers it, the batch path's strips)."""
+    import torch
+
+    from paper_2310_17746_gb300 import binding
+
+    st = torch.cuda.current_stream()
+    rows = []
+    for lo, hi in ((10**14, 10**14 + 10**11), (10**16, 10**16 + 10**10), (10**18, 10**18 + 10**9)):
+        with binding.Sieve(hi) as sv:
+            sv.set_phase_timing(True)
+            out = torch.zeros(2, dtype=torch.int64, device="cuda")
+            rec = {"range": f"[{lo:.0e}, {lo:.0e} + {hi - lo:.0e})", "width": hi - lo}
+            results = []
+            # buckets: the default; no_buckets: every prime located in every
+            # tile (an asynchronous call never leaves the tile path); strips: a
+            # synchronous call with the bucket sieve off, which the planner
+            # may send to the batch path (its host planning is inside the events)
+            for name, opts, asy in (("buckets", {}, True), ("no_buckets", {"bucket_threshold": 0}, True),
+                                    ("strips_route", {"bucket_threshold": 0}, False)):
+                sv.set_options(**opts)
+                sv.range_count(lo, hi, out=out)
+                torch.cuda.synchronize()
+                ts = []
+                for _ in range(max(2, min(steps, 5))):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(st)
+                    sv.range_count(lo, hi, out=out, asynchronous=asy)
+                    b.record(st)
+                    torch.cuda.synchronize()
+                    ts.append(a.elapsed_time(b))
+                results.append((int(out[0]), int(out[1])))
+                rec[name + "_ms"] = round(min(ts), 3)
+                if name == "buckets":
+                    rec["bucket_waves"] = int(sv.phase_times()["bucket_waves"])
+            assert results[0] == results[1] == results[2], (lo, results)
+            rec["count"] = results[0][0]
+            rec["speedup"] = round(min(rec["no_buckets_ms"], rec["strips_route_ms"]) / rec["buckets_ms"], 2)
+            rows.append(rec)
+    return {"metric": "sieved range width/s far up (count)", "ranges": rows}
+
+
 def batch_leg(steps: int, warmup: int) -> dict:
     """Batched range queries/s: the 4096-query workload (seed 0: lo log-uniform
     in [1e6, 1e15], width in [1e3, 1e8], half list mode) in one batched call,
@@ -316,9 +439,29 @@ def batch_leg(steps: int, warmup: int) -> dict:
         t0 = time.perf_counter()
         sv.range_batch(q.lo, q.hi, q.mode, cnt=hc, offsets=ho, values=hv)
         te.append(time.perf_counter() - t0)
+    opts = sv.options()
     sv.close()
+    # roofline: the batch's strikes (expected, see expected_strikes) over its
+    # device time, against the shared-memory atomic-AND rate every strike
+    # uses; and its list bytes against HBM
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    atom_cf, _ = binding.measure_smem_atomics(torch.cuda.current_device())
+    first = LAST_PRESIEVED[opts["presieve_groups"]] + 1
+    strikes = expected_strikes(q.lo, q.hi, first, small_primes(int(math.isqrt(int(q.hi.max())))))
+    atom_peak = props.multi_processor_count * atom_cf * sm_max * 1e6 / 1e9
+    hbm_peak = float(peaks.get("hbm_gbs") or 6800.0)
     return {
         "metric": "batched range queries/s", "value": nq / t_dev, "unit": "queries/s",
+        "roofline": {"bound": "alu", "resource": "shared-memory atomic AND lane operations (the strikes)",
+                     "achieved": strikes / t_dev / 1e9, "peak": atom_peak, "unit": "Gop/s",
+                     "frac": strikes / t_dev / 1e9 / atom_peak, "traffic": None,
+                     "strikes_per_batch": strikes,
+                     "peak_basis": f"measured (sieve_measure_smem_atomics): {atom_cf:.2f} lane-ops/clk/SM x "
+                                   f"{props.multi_processor_count} SMs x {sm_max:.0f} MHz",
+                     "list_bytes_roofline": {"bound": "hbm", "achieved": need * 8 / t_dev / 1e9, "peak": hbm_peak,
+                                             "unit": "GB/s", "frac": need * 8 / t_dev / 1e9 / hbm_peak}},
         "ms_per_batch": 1e3 * t_dev, "queries": nq, "list_primes": need,
         "workload": "4096 queries, seed 0: lo = floor(10^U(6,15)), width = floor(10^U(3,8)), half list mode "
                     "(uint64 primes, CSR), base primes <= 3.2e7 on the device",
@@ -335,10 +478,11 @@ def batch_leg(steps: int, warmup: int) -> dict:
 
 def list_leg(steps: int, warmup: int) -> dict:
     """The list path: the uint64 primes of [1e12, 1e12 + 2e10) written into a
-    device buffer through sieve_range, with the tile kernel and the compaction
-    timed by the library's phase events.  Roofline of the compaction: the HBM
-    bytes it must move (8 B per listed prime written, each tile's bitmap read
-    once) over its device time, against the measured copy bandwidth."""
+    device buffer through sieve_range, two-pass (default: tile kernel writes
+    bitmaps, scan, compaction) and single-pass (each tile compacted from
+    shared memory at an offset found by look-back).  Roofline: the 8 bytes
+    per listed prime the method must write, over the whole call, against the
+    measured copy bandwidth; the compaction kernel's own rate beside it."""
     import numpy as np
     import torch
 
@@ -349,55 +493,60 @@ def list_leg(steps: int, warmup: int) -> dict:
     n = sv.range_count(lo, hi).count
     out = torch.empty(max(n, 1), dtype=torch.int64, device="cuda")
     sv.set_phase_timing(True)
-    for _ in range(max(1, warmup)):
-        sv.range_list(lo, hi, out=out)
     st = torch.cuda.current_stream()
-    calls, phases = [], []
-    for _ in range(steps):
-        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        s.record(st)
-        got = sv.range_list(lo, hi, out=out)
-        e.record(st)
-        torch.cuda.synchronize()
-        calls.append(s.elapsed_time(e) / 1e3)
-        phases.append(sv.phase_times())
-        assert got == n, (got, n)
-    head = out[:4].cpu().numpy()
-    tail = out[n - 2:n].cpu().numpy()
-    assert head[0] == 1000000000039 and (np.diff(head) > 0).all() and tail[-1] < hi, (head, tail)
+    res = {}
+    for sp in (0, 1):
+        sv.set_options(list_single_pass=sp)
+        for _ in range(max(1, warmup)):
+            sv.range_list(lo, hi, out=out)
+        calls, phases = [], []
+        for _ in range(steps):
+            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            s_.record(st)
+            got = sv.range_list(lo, hi, out=out)
+            e_.record(st)
+            torch.cuda.synchronize()
+            calls.append(s_.elapsed_time(e_) / 1e3)
+            phases.append(sv.phase_times())
+            assert got == n, (got, n)
+        head = out[:4].cpu().numpy()
+        tail = out[n - 2:n].cpu().numpy()
+        assert head[0] == 1000000000039 and (np.diff(head) > 0).all() and tail[-1] < hi, (head, tail)
+        res[sp] = (statistics.mean(calls), phases)
     sv.close()
+    t_call, phases = res[0]
     ph = phases[-1]
     compact_s = statistics.mean(p["compact_ms"] for p in phases) / 1e3
     sieve_s = statistics.mean(p["sieve_ms"] for p in phases) / 1e3
     bitmap_bytes = int(ph["tiles"]) * (int(ph["tile_len"]) // 32) * 8
-    alg_bytes = n * 8 + bitmap_bytes
-    achieved = alg_bytes / compact_s / 1e9
     peaks = measured_peaks()
     peak = float(peaks.get("hbm_gbs") or 6800.0)
+    alg_bytes = n * 8
+    achieved = alg_bytes / t_call / 1e9
     per_prime = profiled_traffic("compact_kernel_list_1e12.json", "dram_bytes_per_listed_prime")
     return {
-        "metric": "listed primes/s", "value": n / statistics.mean(calls), "unit": "primes/s",
+        "metric": "listed primes/s", "value": n / t_call, "unit": "primes/s",
         "workload": "the uint64 primes of [1e12, 1e12 + 2e10) into a device buffer (sieve_range, list mode)",
-        "primes": n, "ms_per_call": 1e3 * statistics.mean(calls),
+        "primes": n, "ms_per_call": 1e3 * t_call,
         "tile_kernel_ms": 1e3 * sieve_s, "compaction_ms": 1e3 * compact_s,
-        "roofline": {"bound": "hbm", "kernel": "compact_kernel", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": per_prime * n if per_prime else None,
-                     "algorithmic_bytes": alg_bytes,
+        "single_pass_ms_per_call": 1e3 * res[1][0],
+        "roofline": {"bound": "hbm", "kernel": "range_tiles_kernel + compact_kernel (whole call)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": per_prime * n if per_prime else None, "algorithmic_bytes": alg_bytes,
                      "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json)" if peaks.get("hbm_gbs")
-                     else "fallback 6.8 TB/s"},
+                     else "fallback 6.8 TB/s",
+                     "compaction_kernel_gbs": (alg_bytes + bitmap_bytes) / compact_s / 1e9},
         "l2": "output (5.8 GB) exceeds L2; no flush",
     }
 
 
-def serving_leg(rates=(1000, 3000, 10000, 30000, 100000), seconds: float = 1.0, max_n: int = 40000,
-                naive_rates: int = 2) -> dict:
+def serving_leg(rates=(1000, 3000, 10000, 30000, 100000), seconds: float = 1.0, max_n: int = 10000) -> dict:
     """Open-loop Poisson request streams (seed 1: lo log-uniform in [1e6, 1e18],
     width in [1e3, 1e9], 20% list mode) against the continuous-batching server;
     latency = submit to result ready on the server.  Results are collected into
-    device memory.  Compared with one range launch per request in arrival order
-    at the lowest rates."""
+    device memory.  Compared, at every offered rate and with the same requests,
+    with one range launch per request in arrival order."""
     import threading as th
 
     import numpy as np
@@ -465,10 +614,10 @@ def serving_leg(rates=(1000, 3000, 10000, 30000, 100000), seconds: float = 1.0, 
             "p99_us": st["p99_us"], "mean_us": st["mean_us"], "max_us": st["max_us"],
             "batches": st["batches"], "mean_batch": st["mean_batch"], "overlapped_batches": st["overlapped_batches"]})
     srv.stop()
-    # one range launch per request, in arrival order, at the lowest rates
+    # one range launch per request, in arrival order, same requests at every rate
     naive = []
-    for rate in rates[:naive_rates]:
-        n = int(min(2000, rate * seconds))
+    for rate in rates:
+        n = int(min(max_n, rate * seconds))
         arr = workloads.serving_arrivals(float(rate), n, seed=1)
         lat = []
         t0 = time.perf_counter()
@@ -510,6 +659,20 @@ def run_gpu(args):
     lo, hi = rank_range(rank)
     stream = torch.cuda.current_stream(dev)
     sv = binding.Sieve(hi, device=local, stream=stream.cuda_stream)
+    # the tunables: from the tuning cache for this device and workload, or
+    # tuned now on a 2e10-wide sample of the range (and stored by rank 0)
+    t0 = time.perf_counter()
+    got = sv.tune_cache_load(TUNE_CACHE, TUNE_WORKLOAD)
+    if got is None:
+        mid = lo + (hi - lo) // 2
+        tuned, tuned_ms = sv.autotune_range(mid, mid + 2 * 10**10, reps=2)
+        tune_source = "tuned in this run on [mid, mid + 2e10) of the range"
+        if rank == 0:
+            sv.tune_cache_store(TUNE_CACHE, TUNE_WORKLOAD, tuned_ms)
+    else:
+        tuned, tuned_ms = got
+        tune_source = "tuning cache " + os.path.relpath(TUNE_CACHE, ROOT)
+    tune_s = time.perf_counter() - t0
     nb = binding.Sieve.nbins(lo, hi, SEG_WIDTH)
     counts = torch.zeros(nb, dtype=torch.int64, device=dev)
     total = torch.zeros(2, dtype=torch.int64, device=dev)
@@ -589,7 +752,11 @@ def run_gpu(args):
     peak = props.multi_processor_count * atom_cf * sm_max * 1e6 / 1e9
     traffic = profiled_traffic("range_tiles_count_1e12.json")
 
-    batch = serving = listing = None
+    batch = serving = listing = naive = far = None
+    if world == 1 and not args.no_naive:
+        naive = naive_leg()
+    if world == 1 and not args.no_far:
+        far = far_leg(args.steps)
     if world == 1 and not args.no_batch:
         batch = batch_leg(args.steps, args.warmup)
     if world == 1 and not args.no_list:
@@ -612,6 +779,10 @@ def run_gpu(args):
                    "lo": lo, "hi_exclusive": hi, "seg_width": SEG_WIDTH,
                    "tile_bits": opts["tile_bits"], "block_threads": opts["block_threads"],
                    "group_hits": opts["group_hits"],
+                   "autotuned": {"options": {k: opts[k] for k in ("tile_bits", "block_threads", "ctas_per_sm",
+                                                                  "group_hits", "presieve_groups",
+                                                                  "bucket_threshold")},
+                                 "source": tune_source, "tuned_sample_ms": tuned_ms, "seconds": tune_s},
                    "l2": "flushed between steps (256 MiB write outside the timed events)"},
         "check": {"pi_1e12": got_count, "expected": PI_1E12, "ok": got_count == PI_1E12},
         "roofline": {"bound": "alu", "resource": "shared-memory atomic AND lane operations (the strikes)",
@@ -627,6 +798,12 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16,
                 "d2h_bytes_per_step": 8 * nb + 16},
         "gpu_launches": launches,
+        "naive_gpu": (None if naive is None else
+                      {"value": naive["configs"][-1]["naive_numbers_per_s"], "unit": UNIT,
+                       "ms": naive["configs"][-1]["naive_ms"],
+                       "headline_speedup": (naive["configs"][-1]["naive_ms"] / (1e3 * t_max / args.steps)),
+                       "all": naive}),
+        "far": far,
         "batch": batch,
         "list": listing,
         "serving": serving,

@@ -264,7 +264,8 @@ int sieve_range_each(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, con
  *     ranges to come; every candidate sieves it reps + 1 times); then, when
  *     the range's large primes can use the bucket sieve, bucket_threshold
  *     {0, 2, 4, 8, 16} x bucket_wave {1, 4} x bucket_scatter {1, 2} with the
- *     winner's other settings. */
+ *     winner's other settings.  The context's own options stay when they are
+ *     among the candidates and within 1% of the fastest (run-to-run noise). */
 int sieve_autotune_batch(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, const uint8_t *mode, size_t nq,
                          int reps, sieve_options *best, double *best_ms);
 int sieve_autotune_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, int reps, sieve_options *best,

@@ -145,6 +145,7 @@ extern "C" int sieve_autotune_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, in
   double best_t = 1e300;
   sieve_count_result ref{0, 0}, got{0, 0};
   bool have_ref = false;
+  double orig_t = 1e300;  // time of the context's own options, when among the candidates
   // times each candidate (reps runs after an untimed one) and keeps the
   // fastest; every candidate's result must equal the first one's
   auto try_all = [&](const std::vector<sieve_options> &cand) {
@@ -181,6 +182,7 @@ extern "C" int sieve_autotune_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, in
         return;
       }
       const double t = median(ts);
+      if (memcmp(&o, &orig, sizeof(o)) == 0) orig_t = t;
       if (t < best_t) {
         best_t = t;
         best_opt = o;
@@ -242,6 +244,12 @@ extern "C" int sieve_autotune_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, in
             bc.push_back(o);
           }
       try_all(bc);
+    }
+    // keep the context's options when they are within 1% of the fastest
+    // candidate: such a gap is within run-to-run noise
+    if (orig_t <= 1.01 * best_t) {
+      best_opt = orig;
+      best_t = orig_t;
     }
   } while (0);
   cudaFree(d_tot);
