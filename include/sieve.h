@@ -206,6 +206,47 @@ int sieve_segment_counts(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t seg_
  * stale.  Errors: INVALID, RANGE (past 2^63), OOM, CUDA. */
 int sieve_next(sieve_ctx *ctx, uint64_t after, size_t k, uint64_t *out, size_t *n_out, unsigned flags);
 
+/* ------------------------------------------------------------- long runs */
+
+/* The paper's first future-work item (Section 6) is to write results out in
+ * store segments instead of keeping them in memory; these two calls do that
+ * for counts and for lists, and survive interruption.  Their state files are
+ * small binary records (8 magic bytes, little-endian uint64 words, a 64-bit
+ * FNV-1a hash of the preceding bytes), written to path + ".tmp" and renamed
+ * over the old record after every chunk, so a crash leaves the old or the new
+ * record, never a torn one.
+ *
+ * sieve_count_checkpointed: count, checksum and per-segment counts of
+ * [lo, hi) (segments as sieve_segment_counts; seg_width 0 = no segments and
+ * ncounts 0), sieved in chunks [lo + k chunk_width, lo + (k + 1) chunk_width).
+ * After every chunk the running state (next position, count, checksum, bins)
+ * goes to state_path.  A call that finds a state for the same (lo, hi,
+ * seg_width, chunk_width) resumes after its last finished chunk; a state of
+ * another job, or a damaged one, is INVALID.  max_chunks > 0 stops after that
+ * many chunks of this call and returns SIEVE_PENDING with the partial totals
+ * (call again to continue); 0 runs to the end.  When the range is done the
+ * call returns SIEVE_OK with *total and counts[] (host memory) complete, and
+ * a later call with the same state returns them without sieving.  *next (may
+ * be NULL) gets the start of the first chunk not yet done. */
+int sieve_count_checkpointed(sieve_ctx *ctx, uint64_t lo, uint64_t hi, uint64_t seg_width, uint64_t chunk_width,
+                             const char *state_path, uint64_t *counts, size_t ncounts,
+                             sieve_count_result *total, uint64_t max_chunks, uint64_t *next);
+
+/* The primes of [lo, hi), increasing, as little-endian uint64 in the binary
+ * file `path`, written one store segment at a time: a window of the range
+ * whose prime count is surely <= segment_primes (0 = 125,000,000, i.e. 1 GB
+ * of output per segment) is sieved into device memory, copied to pinned host
+ * memory and appended, then path + ".state" records the next position and
+ * the primes written.  resume != 0 continues from that state (the file is
+ * cut back to the primes the state records, dropping what an interrupted
+ * segment left); resume == 0 starts a new file.  max_segments > 0 stops after
+ * that many segments of this call with SIEVE_PENDING.  *n_written (may be
+ * NULL) = primes in the file.  Uses segment_primes x 8 bytes of device memory
+ * and as much pinned host memory, allocated and freed by the call.  Errors:
+ * INVALID (bad argument, file error, state of another job), RANGE, OOM, CUDA. */
+int sieve_primes_to_file(sieve_ctx *ctx, uint64_t lo, uint64_t hi, const char *path, size_t segment_primes,
+                         int resume, uint64_t max_segments, uint64_t *n_written);
+
 /* ------------------------------------------------------------- batches */
 
 /* Many independent ranges in one call: query i is [lo[i], hi[i]) in mode

@@ -126,6 +126,9 @@ SIGNATURES = {
     "sieve_set_phase_timing": (_i, [_p, _i]),
     "sieve_get_phase_times": (_i, [_p, _p]),
     "sieve_next": (_i, [_p, _u64, _sz, _p, ctypes.POINTER(_sz), _u]),
+    "sieve_count_checkpointed": (_i, [_p, _u64, _u64, _u64, _u64, ctypes.c_char_p, _p, _sz, _p, _u64,
+                                      ctypes.POINTER(_u64)]),
+    "sieve_primes_to_file": (_i, [_p, _u64, _u64, ctypes.c_char_p, _sz, _i, _u64, ctypes.POINTER(_u64)]),
     "sieve_range_naive": (_i, [_p, _u64, _u64, _i, _p, _p, _sz, ctypes.POINTER(_sz), _u]),
     "sieve_tune_cache_store": (_i, [_p, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_double]),
     "sieve_tune_cache_load": (_i, [_p, ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(_i),
@@ -481,6 +484,31 @@ class Sieve:
         _check(self._lib.sieve_autotune_range(self._h, int(lo), int(hi), int(reps), ctypes.byref(o),
                                               ctypes.byref(ms)), "sieve_autotune_range")
         return o.as_dict(), float(ms.value)
+
+    def count_checkpointed(self, lo: int, hi: int, seg_width: int, chunk_width: int, state_path: str,
+                           max_chunks: int = 0):
+        """Checkpointed count of [lo, hi) (sieve_count_checkpointed).  Returns
+        (done, CountAndSum, bins, next): done is False when max_chunks stopped
+        the call early (the state file holds the progress)."""
+        nb = self.nbins(lo, hi, seg_width) if seg_width else 0
+        bins = np.zeros(max(nb, 1), dtype=np.uint64)
+        r = CountResult()
+        nxt = _u64(0)
+        rc = self._lib.sieve_count_checkpointed(self._h, int(lo), int(hi), int(seg_width), int(chunk_width),
+                                                str(state_path).encode(), bins.ctypes.data, nb,
+                                                ctypes.cast(ctypes.byref(r), _p), int(max_chunks), ctypes.byref(nxt))
+        _check(rc, "sieve_count_checkpointed")
+        return rc == OK, CountAndSum(r.count, r.checksum), bins[:nb], int(nxt.value)
+
+    def primes_to_file(self, lo: int, hi: int, path: str, segment_primes: int = 0, resume: bool = False,
+                       max_segments: int = 0):
+        """Primes of [lo, hi) spilled to the uint64 file `path` in store
+        segments (sieve_primes_to_file).  Returns (done, primes written)."""
+        n = _u64(0)
+        rc = self._lib.sieve_primes_to_file(self._h, int(lo), int(hi), str(path).encode(), int(segment_primes),
+                                            1 if resume else 0, int(max_segments), ctypes.byref(n))
+        _check(rc, "sieve_primes_to_file")
+        return rc == OK, int(n.value)
 
     def tune_cache_store(self, path: str, workload: str, ms: float = 0.0) -> None:
         """Save the context's current options in the JSON tuning cache at
