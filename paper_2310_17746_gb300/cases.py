@@ -6,8 +6,9 @@
   python -m paper_2310_17746_gb300.cases batch  NQ [--seed S] [--count-only] [--mix batch|serving] [--reps R]
 
 Numbers accept Python expressions such as 10**10+1 or 2**30.  Options may
-set tile_bits / block_threads / group_hits.  Prints one line per repetition
-with the CUDA-event time of the call.
+set tile_bits / block_threads / group_hits / presieve_groups, the bucket
+sieve's threshold, wave and scatter kind, and the one-pass list.  Prints one
+line per repetition with the CUDA-event time of the call.
 """
 from __future__ import annotations
 
@@ -33,6 +34,11 @@ def main(argv=None) -> int:
     ap.add_argument("--tile-bits", type=_num, default=0)
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--group-hits", type=int, default=0)
+    ap.add_argument("--presieve-groups", type=int, default=-1)
+    ap.add_argument("--bucket-threshold", type=int, default=-1, help="0 turns the bucket sieve off")
+    ap.add_argument("--bucket-wave", type=int, default=0)
+    ap.add_argument("--bucket-scatter", type=int, default=-1, help="0 automatic, 1 direct, 2 sorted")
+    ap.add_argument("--single-pass", type=int, default=-1, help="list: 1 one pass, 0 two passes")
     ap.add_argument("--batch-tile-bits", type=_num, default=0)
     ap.add_argument("--chunk-primes", type=_num, default=0)
     ap.add_argument("--seed", type=int, default=0)
@@ -49,7 +55,11 @@ def main(argv=None) -> int:
     lo = args.a if args.kind in ("count", "list") else 0
     sv = binding.Sieve(max(hi, 2))
     opts = {k: v for k, v in (("tile_bits", args.tile_bits), ("block_threads", args.block_threads),
-                              ("group_hits", args.group_hits)) if v}
+                              ("group_hits", args.group_hits), ("bucket_wave", args.bucket_wave)) if v}
+    opts.update({k: v for k, v in (("presieve_groups", args.presieve_groups),
+                                   ("bucket_threshold", args.bucket_threshold),
+                                   ("bucket_scatter", args.bucket_scatter),
+                                   ("list_single_pass", args.single_pass)) if v >= 0})
     if opts:
         sv.set_options(**opts)
     dev = torch.device("cuda")
