@@ -112,7 +112,7 @@ def algorithmic_ops(lo: int, hi: int, first: int = 23) -> dict:
 def source_hash() -> str:
     h = hashlib.sha256()
     # the files the count kernel is compiled from
-    for name in ("range.cu", "tile.cuh", "sieve_internal.cuh", "api.cu"):  # api.cu: the default options
+    for name in ("range.cu", "tile.cuh", "bucket.cuh", "sieve_internal.cuh", "api.cu"):  # api.cu: the default options
         f = os.path.join(ROOT, "paper_2310_17746_gb300", "csrc", name)
         with open(f, "rb") as fh:
             h.update(fh.read())

@@ -97,10 +97,10 @@ def test_bucket_overflow_falls_back(sv, base, scatter):
 
 
 def test_far_ranges_route_to_buckets(sv, base):
-    """sieve_range keeps a far range on the tile path when the bucket sieve
-    applies (instead of the batch path's strips); both routes agree with the
-    oracle."""
-    lo, hi = 10**15 - 3 * 10**8, 10**15
+    """sieve_range keeps a far range whose bitmap would not fit in L2 on the
+    tile path when the bucket sieve applies (instead of the batch path's
+    strips); both routes agree with the oracle."""
+    lo, hi = 10**15 - 3 * 10**9, 10**15
     r = sv.range_count(lo, hi)
     assert sv.phase_times()["bucket_waves"] > 0
     old = sv.options()
