@@ -659,7 +659,13 @@ extern "C" int sieve_primes_u32(sieve_ctx *ctx, uint64_t n, uint32_t *out, size_
 // length once per tile costs more than locating them once and clearing their
 // hits with global atomics (priced 4x higher when the range's bitmap would
 // not fit half of L2).
-constexpr uint64_t kStripBitmapL2 = 48000000;  // bytes of a range's two class bitmaps that stay in L2
+namespace sieve {
+bool strips_beat_buckets(uint64_t lo, uint64_t hi) {
+  if (hi <= lo) return false;
+  const uint64_t span = (hi + 4) / 6 - lo / 6;
+  return span / 4 <= kStripBitmapL2 && hi - lo >= 300000000ull && isqrt_u64(hi - 1) >= 100000000ull;
+}
+}  // namespace sieve
 
 static bool strips_pay_off(const sieve_ctx *ctx, uint64_t lo, uint64_t hi) {
   if (hi <= lo || hi > (1ull << 63)) return false;
@@ -706,12 +712,10 @@ extern "C" int sieve_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, int mode, s
   rq.out_on_device = (flags & SIEVE_OUT_DEVICE) != 0;
   rq.total = cnt;
   rq.async = mode == SIEVE_COUNT && (flags & SIEVE_OUT_DEVICE) && (flags & SIEVE_ASYNC);
-  // far ranges: the batch path's strips when they pay off and the range's
-  // bitmap fits in L2 (their atomic ANDs then stay on chip: [1e18, +1e9)
-  // 1.2 ms against 2.1 ms for the bucket sieve), else the bucket sieve when it
+  // far ranges: the batch path's strips when they pay off and beat the bucket
+  // sieve ([1e18, +1e9): 1.2 ms against 2.1 ms), else the bucket sieve where it
   // applies ([1e16, +1e10): 8.6 ms against 22.8 ms through strips)
-  const bool bitmap_in_l2 = hi > lo && ((hi + 4) / 6 - lo / 6) / 4 <= kStripBitmapL2;
-  if (!rq.async && strips_pay_off(ctx, lo, hi) && (bitmap_in_l2 || !range_prefers_buckets(ctx, lo, hi))) {
+  if (!rq.async && strips_pay_off(ctx, lo, hi) && (strips_beat_buckets(lo, hi) || !range_prefers_buckets(ctx, lo, hi))) {
     // a range far up: run it as a one-query batch, whose planner locates the
     // primes above the tile length once for the whole range (strips) instead
     // of once per tile

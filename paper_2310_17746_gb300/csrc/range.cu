@@ -599,8 +599,16 @@ static int range_geometry(const sieve_ctx *ctx, const DeviceTable &table, uint64
     if (lw < L) L = lw;
   }
   int per_sm = 0;
-  int rc = dispatch_occupancy(g->threads, &per_sm, list, (size_t)L / 4);
-  if (rc != SIEVE_OK) return rc;
+  const int ti = g->threads == 256 ? 0 : (g->threads == 512 ? 1 : 2);
+  const uint32_t lg = log2u(L) & 31;
+  int *cached = const_cast<int *>(&ctx->occ_cache[ti][list ? 1 : 0][lg]);
+  if (*cached > 0) {
+    per_sm = *cached;
+  } else {
+    int rc = dispatch_occupancy(g->threads, &per_sm, list, (size_t)L / 4);
+    if (rc != SIEVE_OK) return rc;
+    if (per_sm > 0) *cached = per_sm;
+  }
   if (per_sm < 1) {
     set_error("tile of %u bits does not fit on an SM", L);
     return SIEVE_ERR_INVALID;

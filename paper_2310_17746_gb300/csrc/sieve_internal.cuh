@@ -304,6 +304,9 @@ struct sieve_ctx {
   // growable device staging for list output bound for host memory
   void *d_stage = nullptr;
   size_t stage_bytes = 0;
+  // resident CTAs per SM of the range kernels, by (threads 256/512/1024,
+  // list mode, log2 of the tile length); 0 = not asked yet (range.cu)
+  int occ_cache[3][2][32] = {};
   // bucket sieve buffers of single-range calls (entries, counts, overflow
   // flags), kept across calls and grown on demand (range.cu)
   void *d_bucket = nullptr;
@@ -386,5 +389,19 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
 // path instead of routing it to the batch path's strips (the buckets measured
 // faster on every far range tried).
 bool range_prefers_buckets(sieve_ctx *ctx, uint64_t lo, uint64_t hi);
+
+// Bytes of a range's two class bitmaps up to which they stay in L2: below it
+// the batch path's strips (atomic ANDs into the bitmap) beat the bucket sieve
+// for a far range, above it the bucket sieve wins (measured both ways).
+constexpr uint64_t kStripBitmapL2 = 48000000;
+
+// Whether the batch path's strips beat the bucket sieve on a far range:
+// measured on one GB300 (counts, widths 1e8..1e9 and 1e10, lo 1e12..1e18),
+// they do when the range's bitmap fits in L2, the range is at least 3e8 wide
+// and its base primes reach 1e8 (lo above about 1e16): a single pass of
+// locations over tens of millions of primes and L2-resident atomic ANDs cost
+// less than the bucket entries' round trip.  Below that the bucket sieve is
+// faster (e.g. [1e15, 1e15 + 1e8): 0.13 against 0.30 ms) or equal (api.cu).
+bool strips_beat_buckets(uint64_t lo, uint64_t hi);
 
 }  // namespace sieve

@@ -82,25 +82,26 @@ def test_window_1e18_oracle():
 
 
 def test_far_range_routes_and_matches():
-    """A range far up ([1e18, 1e18 + 2e7): 7 tiles, 5e7 base primes, a bitmap
-    that fits in L2) goes to the batch path's strips (a one-query batch); the
-    same range through the bucket sieve (one segment-path launch,
-    range_batch(naive=True)) and tile by tile with the bucket sieve off must
-    give the same counts and lists, equal to the oracle's."""
+    """A range far up ([1e18, 1e18 + 2e7): 5e7 base primes) goes through the
+    bucket sieve by default; with the bucket sieve off, sieve_range sends it to
+    the batch path's strips (a one-query batch); and one segment-path launch
+    with the bucket sieve off (range_batch(naive=True)) locates every prime in
+    every tile.  All three must give the same counts and lists, equal to the
+    oracle's."""
     _need_gpu()
     lo, hi = 10**18, 10**18 + 2 * 10**7
     with binding.Sieve(hi) as sv:
         sv.set_phase_timing(True)
         got = sv.range_count(lo, hi)
-        lst = sv.range_list(lo, hi)
-        assert sv.phase_times()["bucket_waves"] == 0  # not the segment path
-        cnt_b, off_b, vals_b = sv.range_batch([lo], [hi], [1], naive=True)
         assert sv.phase_times()["bucket_waves"] > 0
+        lst = sv.range_list(lo, hi)
         sv.set_options(bucket_threshold=0)
+        strips = sv.range_count(lo, hi)
+        lst_s = sv.range_list(lo, hi)
         cnt_e, off_e, vals_e = sv.range_batch([lo], [hi], [1], naive=True)
-    assert (got.count, got.checksum) == (int(cnt_b[0][0]), int(cnt_b[0][1])) == (int(cnt_e[0][0]), int(cnt_e[0][1]))
-    np.testing.assert_array_equal(lst, vals_b)
+    assert (got.count, got.checksum) == (strips.count, strips.checksum) == (int(cnt_e[0][0]), int(cnt_e[0][1]))
     np.testing.assert_array_equal(lst, vals_e)
+    np.testing.assert_array_equal(lst_s, vals_e)
     want = oracle.count_range(lo, hi)
     assert (got.count, got.checksum) == want
     assert lst.size == want[0]
