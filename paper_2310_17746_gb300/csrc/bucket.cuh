@@ -241,13 +241,27 @@ __global__ void __launch_bounds__(SB) bucket_scatter_direct_kernel(const BucketP
     uint32_t a1, a5;
     starts_from_inverse(K0, P, __ldg(b.magic + i), __ldg(b.cinv + i), a1, a5);
     const uint32_t base = (uint32_t)(K0 - Kw);
-    for (uint32_t k = base + a1; k < wlen; k += P) emit(k, 0);
-    for (uint32_t k = base + a5; k < wlen; k += P) emit(k, 1);
+    // four hits per trip: their slot atomics are independent, so they are in
+    // flight together instead of one at a time (64-bit index: k + 3P may pass
+    // 2^32 before the test ends the loop)
+    auto walk = [&](uint64_t k, uint32_t cls) {
+      for (; k + 3ull * P < wlen; k += 4ull * P) {
+        emit((uint32_t)k, cls);
+        emit((uint32_t)(k + P), cls);
+        emit((uint32_t)(k + 2ull * P), cls);
+        emit((uint32_t)(k + 3ull * P), cls);
+      }
+      for (; k < wlen; k += P) emit((uint32_t)k, cls);
+    };
+    walk(base + a1, 0);
+    walk(base + a5, 1);
   }
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < ntl; i += SB)
     b.counts[(size_t)i * b.ncta + blockIdx.x] = sub[i] < b.cap ? sub[i] : b.cap;
 }
+
+constexpr int kDrainUnroll = 8;
 
 // Drain the buckets of wave tile `tl` into the tile's bitmaps: warp w takes
 // the sub-buckets w, w + NWARPS, ...; its lanes read consecutive entries.
@@ -259,9 +273,9 @@ __device__ __forceinline__ void bucket_drain(uint32_t *s1, uint32_t *s5, const T
   const uint32_t wmask = tg.W - 1, logW = tg.logW, len = tg.len;
   const uint32_t *cnt = b.counts + (size_t)tl * b.ncta;
   const uint32_t *ent = b.entries + (size_t)tl * b.ncta * b.cap;
-  // four loads in flight per lane before the strikes (the entries come from
-  // L2 or DRAM; one at a time the loop waits on each); a slot past the
-  // sub-bucket's count reads as an index >= len and strikes nothing
+  // kDrainUnroll loads in flight per lane before the strikes (the entries
+  // come from L2 or DRAM; one at a time the loop waits on each); a slot past
+  // the sub-bucket's count reads as an index >= len and strikes nothing
   auto hit = [&](uint32_t v) {
     const uint32_t k = v >> 1;
     if (k < len) strike_one((v & 1) ? s5 : s1, k, wmask, logW);
@@ -269,15 +283,12 @@ __device__ __forceinline__ void bucket_drain(uint32_t *s1, uint32_t *s5, const T
   for (uint32_t c = warp; c < b.ncta; c += NWARPS) {
     const uint32_t n = __ldg(cnt + c);
     const uint32_t *e = ent + (size_t)c * b.cap;
-    for (uint32_t q = lane; q < n; q += 128) {  // read once: streaming loads
-      const uint32_t v0 = __ldcs(e + q);
-      const uint32_t v1 = q + 32 < n ? __ldcs(e + q + 32) : 0xFFFFFFFFu;
-      const uint32_t v2 = q + 64 < n ? __ldcs(e + q + 64) : 0xFFFFFFFFu;
-      const uint32_t v3 = q + 96 < n ? __ldcs(e + q + 96) : 0xFFFFFFFFu;
-      hit(v0);
-      hit(v1);
-      hit(v2);
-      hit(v3);
+    for (uint32_t q = lane; q < n; q += 32 * kDrainUnroll) {  // read once: streaming loads
+      uint32_t v[kDrainUnroll];
+#pragma unroll
+      for (int u = 0; u < kDrainUnroll; u++) v[u] = q + 32 * u < n ? __ldcs(e + q + 32 * u) : 0xFFFFFFFFu;
+#pragma unroll
+      for (int u = 0; u < kDrainUnroll; u++) hit(v[u]);
     }
   }
 }
