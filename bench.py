@@ -112,7 +112,7 @@ def algorithmic_ops(lo: int, hi: int, first: int = 23) -> dict:
 def source_hash() -> str:
     h = hashlib.sha256()
     # the files the count kernel is compiled from
-    for name in ("range.cu", "tile.cuh", "bucket.cuh", "sieve_internal.cuh", "api.cu"):  # api.cu: the default options
+    for name in ("range.cu", "tile.cuh", "bucket.cuh", "cluster.cuh", "sieve_internal.cuh", "api.cu"):  # api.cu: the defaults
         f = os.path.join(ROOT, "paper_2310_17746_gb300", "csrc", name)
         with open(f, "rb") as fh:
             h.update(fh.read())
@@ -341,7 +341,8 @@ def far_leg(steps: int) -> dict:
     """Far ranges through sieve_range (count, device output): the default
     path (large primes through the bucket sieve) against the same call with
     the bucket sieve off (every prime located in every tile, or, where the
-    planner prefers it, the batch path's strips)."""
+    planner prefers it, the batch path's strips) and through cluster segments
+    of 16 CTAs."""
     import torch
 
     from paper_2310_17746_gb300 import binding
@@ -358,8 +359,11 @@ def far_leg(steps: int) -> dict:
             # tile (an asynchronous call never leaves the tile path); strips: a
             # synchronous call with the bucket sieve off, which the planner
             # may send to the batch path (its host planning is inside the events)
+            # cluster: the primes above 4 L located once per segment of 16
+            # tiles and struck through distributed shared memory (cluster.cuh)
             for name, opts, asy in (("buckets", {}, True), ("no_buckets", {"bucket_threshold": 0}, True),
-                                    ("strips_route", {"bucket_threshold": 0}, False)):
+                                    ("strips_route", {"bucket_threshold": 0}, False),
+                                    ("cluster", {"cluster_ctas": 16, "cluster_threshold": 4}, True)):
                 sv.set_options(**opts)
                 sv.range_count(lo, hi, out=out)
                 torch.cuda.synchronize()
@@ -375,7 +379,7 @@ def far_leg(steps: int) -> dict:
                 rec[name + "_ms"] = round(min(ts), 3)
                 if name == "buckets":
                     rec["bucket_waves"] = int(sv.phase_times()["bucket_waves"])
-            assert results[0] == results[1] == results[2], (lo, results)
+            assert results[0] == results[1] == results[2] == results[3], (lo, results)
             rec["count"] = results[0][0]
             rec["speedup"] = round(min(rec["no_buckets_ms"], rec["strips_route_ms"]) / rec["buckets_ms"], 2)
             rows.append(rec)

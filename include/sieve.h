@@ -110,6 +110,20 @@ typedef struct {
                               the tiles before it), 0 = two passes (bitmaps to global memory,
                               scan, compaction; the default, measured faster); host-bound
                               lists always take two passes                                    */
+  uint32_t cluster_ctas;   /* single ranges: 0 = off; 2, 4, 8 or 16 = cluster segments (Sections
+                              2.2-2.3 with the chunk spread over a thread-block cluster): C CTAs
+                              sieve C consecutive tiles together, the base primes above
+                              cluster_threshold x tile_bits are located once per segment and
+                              struck into the member CTAs' shared memory through distributed
+                              shared memory.  Replaces the bucket sieve and the far-range
+                              strips route for the call; single-pass lists and ranges whose
+                              base primes reach 2^31 keep their usual route.  Measured slower
+                              than the bucket sieve on a GB300 (remote shared-memory ANDs run
+                              at a small fraction of the local rate); 16 needs a device that
+                              allows clusters beyond the portable size of 8                   */
+  uint32_t cluster_threshold; /* cluster segments: base primes above cluster_threshold x tile_bits
+                              are located once per segment (0: every one-lane prime); at most
+                              1024                                                           */
 } sieve_options;
 
 /* ---------------------------------------------------------------- context */
@@ -454,6 +468,7 @@ typedef struct {
   uint64_t tile_len;  /* indices per residue class per tile */
   uint64_t listed;    /* list mode: primes the compaction wrote */
   uint64_t bucket_waves; /* waves of the bucket sieve (0: not used) */
+  uint64_t cluster_ctas; /* CTAs per cluster of the cluster segments (0: not used) */
 } sieve_phase_times;
 
 /* enable != 0 turns phase timing on (creating the events), 0 turns it off.

@@ -53,7 +53,8 @@ class Options(ctypes.Structure):
                 ("presieve_groups", ctypes.c_uint32), ("batch_tile_bits", ctypes.c_uint32),
                 ("chunk_primes", ctypes.c_uint32), ("bucket_threshold", ctypes.c_uint32),
                 ("bucket_wave", ctypes.c_uint32), ("bucket_scatter", ctypes.c_uint32),
-                ("list_single_pass", ctypes.c_uint32)]
+                ("list_single_pass", ctypes.c_uint32), ("cluster_ctas", ctypes.c_uint32),
+                ("cluster_threshold", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {"tile_bits": self.tile_bits, "block_threads": self.block_threads,
@@ -61,7 +62,8 @@ class Options(ctypes.Structure):
                 "presieve_groups": self.presieve_groups, "batch_tile_bits": self.batch_tile_bits,
                 "chunk_primes": self.chunk_primes, "bucket_threshold": self.bucket_threshold,
                 "bucket_wave": self.bucket_wave, "bucket_scatter": self.bucket_scatter,
-                "list_single_pass": self.list_single_pass}
+                "list_single_pass": self.list_single_pass, "cluster_ctas": self.cluster_ctas,
+                "cluster_threshold": self.cluster_threshold}
 
 
 class ServerConfig(ctypes.Structure):
@@ -72,7 +74,7 @@ class ServerConfig(ctypes.Structure):
 class PhaseTimes(ctypes.Structure):
     _fields_ = [("sieve_ms", ctypes.c_double), ("scan_ms", ctypes.c_double), ("compact_ms", ctypes.c_double),
                 ("tiles", ctypes.c_uint64), ("tile_len", ctypes.c_uint64), ("listed", ctypes.c_uint64),
-                ("bucket_waves", ctypes.c_uint64)]
+                ("bucket_waves", ctypes.c_uint64), ("cluster_ctas", ctypes.c_uint64)]
 
 
 class ServerStats(ctypes.Structure):

@@ -39,6 +39,8 @@ def main(argv=None) -> int:
     ap.add_argument("--bucket-wave", type=int, default=0)
     ap.add_argument("--bucket-scatter", type=int, default=-1, help="0 automatic, 1 direct, 2 sorted")
     ap.add_argument("--single-pass", type=int, default=-1, help="list: 1 one pass, 0 two passes")
+    ap.add_argument("--cluster-ctas", type=int, default=-1, help="0 off, 2/4/8/16: cluster segments")
+    ap.add_argument("--cluster-threshold", type=int, default=-1)
     ap.add_argument("--batch-tile-bits", type=_num, default=0)
     ap.add_argument("--chunk-primes", type=_num, default=0)
     ap.add_argument("--seed", type=int, default=0)
@@ -59,7 +61,9 @@ def main(argv=None) -> int:
     opts.update({k: v for k, v in (("presieve_groups", args.presieve_groups),
                                    ("bucket_threshold", args.bucket_threshold),
                                    ("bucket_scatter", args.bucket_scatter),
-                                   ("list_single_pass", args.single_pass)) if v >= 0})
+                                   ("list_single_pass", args.single_pass),
+                                   ("cluster_ctas", args.cluster_ctas),
+                                   ("cluster_threshold", args.cluster_threshold)) if v >= 0})
     if opts:
         sv.set_options(**opts)
     dev = torch.device("cuda")

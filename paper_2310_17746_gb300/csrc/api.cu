@@ -238,6 +238,8 @@ static sieve_options default_options() {
   o.bucket_wave = 1;
   o.bucket_scatter = 0;    // direct or sorted scatter by the size of a wave's buckets
   o.list_single_pass = 0;  // one pass measured slower: 8.25 vs 6.84 ms for the uint64 list of [1e12, 1e12+2e10)
+  o.cluster_ctas = 0;      // cluster segments off: slower than the bucket sieve ([1e16, +1e10): 19.9 vs 8.5 ms)
+  o.cluster_threshold = 4;  // measured best of 4 / 16 / 64 with 8 and 16 CTAs per cluster
   return o;
 }
 
@@ -286,6 +288,15 @@ static int validate_options(const sieve_ctx *c, const sieve_options &o) {
   }
   if (o.bucket_wave < 1 || o.bucket_wave > 16) {
     set_error("bucket_wave must be in [1, 16]");
+    return SIEVE_ERR_INVALID;
+  }
+  if (o.cluster_ctas != 0 && o.cluster_ctas != 2 && o.cluster_ctas != 4 && o.cluster_ctas != 8 &&
+      o.cluster_ctas != 16) {
+    set_error("cluster_ctas must be 0 (off), 2, 4, 8 or 16");
+    return SIEVE_ERR_INVALID;
+  }
+  if (o.cluster_threshold > 1024) {
+    set_error("cluster_threshold must be in [0, 1024]");
     return SIEVE_ERR_INVALID;
   }
   if (o.presieve_groups > (uint32_t)kMaxPresieveGroups) {
@@ -715,7 +726,9 @@ extern "C" int sieve_range(sieve_ctx *ctx, uint64_t lo, uint64_t hi, int mode, s
   // far ranges: the batch path's strips when they pay off and beat the bucket
   // sieve ([1e18, +1e9): 1.2 ms against 2.1 ms), else the bucket sieve where it
   // applies ([1e16, +1e10): 8.6 ms against 22.8 ms through strips)
-  if (!rq.async && strips_pay_off(ctx, lo, hi) && (strips_beat_buckets(lo, hi) || !range_prefers_buckets(ctx, lo, hi))) {
+  // (cluster segments, when asked for, replace both)
+  if (!rq.async && ctx->opt.cluster_ctas == 0 && strips_pay_off(ctx, lo, hi) &&
+      (strips_beat_buckets(lo, hi) || !range_prefers_buckets(ctx, lo, hi))) {
     // a range far up: run it as a one-query batch, whose planner locates the
     // primes above the tile length once for the whole range (strips) instead
     // of once per tile

@@ -16,6 +16,7 @@
 #include <cuda/atomic>
 
 #include "bucket.cuh"
+#include "cluster.cuh"
 #include "tile.cuh"
 
 namespace sieve {
@@ -53,6 +54,9 @@ struct RangeKernelParams {
   uint64_t cap;                    // elements of out; positions >= cap are not written
   uint32_t out_bytes;
   uint32_t stage_off;              // words from the start of dynamic shared memory to the staging
+  // cluster segments (kLargeCluster)
+  uint32_t cluster;                // CTAs per cluster: C consecutive tiles form one segment
+  uint32_t i_cluster;              // primes with table index >= i_cluster: located once per segment
 };
 
 // What the tile kernel produces: counts only; counts plus each tile's bitmap
@@ -62,6 +66,14 @@ struct RangeKernelParams {
 constexpr int kModeCount = 0;
 constexpr int kModeListBitmap = 1;
 constexpr int kModeListFused = 2;
+
+// How the tile kernel applies the primes far above the tile length: located
+// in every tile; drained from the buckets of a wave (bucket.cuh); or located
+// once per cluster segment and struck through distributed shared memory
+// (cluster.cuh).
+constexpr int kLargeTiles = 0;
+constexpr int kLargeBuckets = 1;
+constexpr int kLargeCluster = 2;
 
 // Decoupled look-back (Merrill & Garland, "Single-pass Parallel Prefix Scan
 // with Decoupled Look-back", 2016) over per-tile words flag << 62 | value:
@@ -135,15 +147,24 @@ __device__ __forceinline__ bool lookback_prefix_warp(unsigned long long *state, 
   return ok;
 }
 
-// BUCKET: the launch sieves the tiles of one bucket wave, [b.t_begin,
-// b.t_begin + b.ntl); the primes with table index >= b.i_large are applied by
-// draining the wave's buckets (bucket.cuh) instead of being located in every
-// tile.  Without BUCKET the launch sieves every tile and b is unused.
-template <int BLOCK, int MODE, bool BUCKET>
+// LARGE = kLargeBuckets: the launch sieves the tiles of one bucket wave,
+// [b.t_begin, b.t_begin + b.ntl); the primes with table index >= b.i_large
+// are applied by draining the wave's buckets (bucket.cuh) instead of being
+// located in every tile.  LARGE = kLargeCluster: the launch is made of
+// clusters of p.cluster CTAs; the CTAs of a cluster take consecutive tiles
+// (one segment) in each step of the grid-stride loop, and the primes with
+// table index >= p.i_cluster are located once per segment (cluster.cuh).  A
+// member whose tile lies past the range's end still takes its share of the
+// segment's primes and both cluster barriers.  Otherwise the launch sieves
+// every tile and b is unused.
+template <int BLOCK, int MODE, int LARGE>
 __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const RangeKernelParams p,
                                                                           const BucketParams b) {
   constexpr bool LIST = MODE == kModeListBitmap;
   constexpr bool FUSED = MODE == kModeListFused;
+  constexpr bool BUCKET = LARGE == kLargeBuckets;
+  constexpr bool CLUSTER = LARGE == kLargeCluster;
+  static_assert(!(CLUSTER && FUSED), "cluster segments take tiles in grid-stride order, not from a counter");
   constexpr int NWARPS = BLOCK / 32;
   extern __shared__ uint32_t smem[];
   const uint32_t W = p.L / 32;
@@ -159,12 +180,14 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
   __shared__ uint32_t sh_tile;                // FUSED: the tile taken next
   __shared__ uint64_t sh_excl;                // FUSED: the tile's output offset
   __shared__ int sh_lb_ok;
+  __shared__ uint32_t sh_np_seg;              // CLUSTER: primes the segment needs
   __shared__ uint64_t red[3 * NWARPS];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t t_begin = BUCKET ? b.t_begin : 0u;
   const uint32_t t_end = BUCKET ? b.t_begin + b.ntl : p.ntiles;
   uint32_t *const counter = FUSED ? p.tile_counter + (BUCKET ? b.wave_id : 0u) : nullptr;
   uint32_t np_prev = 0;  // warp 0: the previous tile's prime count
+  const uint32_t crank = CLUSTER ? cluster_rank() : 0u;
   // tiles in grid-stride order, or (FUSED) from the counter, in increasing
   // order over the CTAs, as the look-back needs
   uint32_t t = t_begin + blockIdx.x;
@@ -179,7 +202,9 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
     sh_poff[threadIdx.x] = pattern_offset(p.k_begin + (uint64_t)t * p.L, p.pd[threadIdx.x]);
   __syncthreads();
 
-  while (t < t_end) {
+  // (a cluster's members share the loop: t - crank is its segment's first tile)
+  while ((CLUSTER ? t - crank : t) < t_end) {
+    const bool active = !CLUSTER || t < t_end;  // CTA-uniform
     const uint64_t K0 = p.k_begin + (uint64_t)t * p.L;
     const uint64_t left = p.k_end - K0;
     TileGeom tg;
@@ -190,7 +215,7 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
     const uint64_t tile_end = B + 6ull * tg.len;
     const uint64_t vend = tile_end < p.hi ? tile_end : p.hi;
 
-    if (warp == 0) {
+    if (warp == 0 && active) {
       // base primes needed: P <= isqrt(vend - 1).  A CTA's tiles go up, so
       // the count of the previous tile stays right unless the next prime
       // joins (then search again).
@@ -224,11 +249,35 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
         }
       }
     }
-    presieve_copy<BLOCK>(s1, s5, tg, K0, p.sliced, p.pd, p.npat, sh_poff);
-    warp_band_starts<BLOCK>(starts, B, tg.len, p.primes, p.magic, p.cinv, p.i_first, p.i_split);
+    // CLUSTER: the segment (the cluster's C tiles from t - crank) and the
+    // primes it needs, by warp 1 of every member
+    uint64_t Ks = 0;
+    uint32_t slen = 0;
+    if (CLUSTER) {
+      Ks = p.k_begin + (uint64_t)(t - crank) * p.L;
+      const uint64_t sleft = p.k_end - Ks, scap = (uint64_t)p.cluster * p.L;
+      slen = (uint32_t)(sleft < scap ? sleft : scap);
+      if (warp == 1) {
+        const uint64_t send = 6 * (Ks + slen), svend = send < p.hi ? send : p.hi;
+        const uint32_t nps = warp_count_le(p.primes, p.nprimes, svend >= 2 ? isqrt_dev(svend - 1) : 0);
+        if (lane == 0) sh_np_seg = nps;
+      }
+    }
+    if (active) {
+      presieve_copy<BLOCK>(s1, s5, tg, K0, p.sliced, p.pd, p.npat, sh_poff);
+      warp_band_starts<BLOCK>(starts, B, tg.len, p.primes, p.magic, p.cinv, p.i_first, p.i_split);
+    }
     __syncthreads();
+    if (CLUSTER) cluster_sync_all();  // every member's tile is presieved before any remote strike
 
-    if (BUCKET) {
+    if (CLUSTER) {
+      // primes below i_cluster in the tile itself, the rest once per segment
+      if (active)
+        strike_primes<BLOCK>(s1, s5, B, tg, p.primes, p.magic, p.cinv, starts, p.i_first, p.i_split, sh_np,
+                             sh_allsq != 0, &sh_next, K0, p.i_cluster);
+      cluster_strike<BLOCK>(s1, s5, p.logW, Ks, slen, crank, p.cluster, p.primes, p.magic, p.cinv, p.i_cluster,
+                            sh_np_seg);
+    } else if (BUCKET) {
       // primes below i_large as usual, the rest from the buckets; a tile whose
       // buckets overflowed also locates the large primes itself (a strike
       // applied twice is harmless)
@@ -242,124 +291,126 @@ __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK) range_tiles_kernel(const 
                            sh_allsq != 0, &sh_next, K0);
     }
     __syncthreads();
+    if (CLUSTER) cluster_sync_all();  // every remote strike into this tile has landed
+    if (active) {
+      // a full tile above the presieved primes and inside [lo, hi) needs no
+      // fix-up (valid_range would give [0, 32 W) in both classes)
+      const bool interior = 6 * K0 > 131 && p.lo <= B + 1 && p.hi >= B + 6ull * 32 * W && tg.len == 32 * W;
+      if (!interior)  // ends with a barrier when it changes the tile
+        fixup_tile<BLOCK>(s1, s5, tg, K0, valid_range(p.lo, p.hi, B, tg.len), p.npat);
 
-    // a full tile above the presieved primes and inside [lo, hi) needs no
-    // fix-up (valid_range would give [0, 32 W) in both classes)
-    const bool interior = 6 * K0 > 131 && p.lo <= B + 1 && p.hi >= B + 6ull * 32 * W && tg.len == 32 * W;
-    if (!interior)  // ends with a barrier when it changes the tile
-      fixup_tile<BLOCK>(s1, s5, tg, K0, valid_range(p.lo, p.hi, B, tg.len), p.npat);
-
-    // popcount, checksum, and the count below the segment boundary (if any).
-    // Word w holds indices w + b W: their values sum to
-    // popc * (6 (K0 + w) + r) + 6 w popc + 6 W * (sum of the set bit positions b),
-    // so a thread accumulates, in 32 bits, the class counts c1 / c5, the
-    // word-weighted count sw and the bit-position sum bs of its words
-    // (sw < 2^15 * 64 * (W / BLOCK) < 2^32), and forms the 64-bit sum once.
-    uint32_t c1 = 0, c5 = 0, sw = 0, below32 = 0;
-    BitPlanes planes;  // the bit-position sum, four word pairs at a time
-    const int has_b = sh_has_boundary;
-    const int64_t t1 = has_b ? sh_t1 : 0, t5 = has_b ? sh_t5 : 0;
-    auto pair = [&](uint32_t w, uint32_t a, uint32_t b) {
-      if (LIST) p.bitmap[(uint64_t)t * W + w] = make_uint2(a, b);
-      const uint32_t ca = __popc(a), cb = __popc(b);
-      c1 += ca;
-      c5 += cb;
-      sw += w * (ca + cb);
-      if (has_b)
-        below32 += __popc(a & below_mask(t1, w, tg.logW, W)) + __popc(b & below_mask(t5, w, tg.logW, W));
-    };
-    uint32_t w = threadIdx.x;
-    for (; w + 3 * BLOCK < W; w += 4 * BLOCK) {
-      const uint32_t a0 = s1[w], b0 = s5[w], a1 = s1[w + BLOCK], b1 = s5[w + BLOCK];
-      const uint32_t a2 = s1[w + 2 * BLOCK], b2 = s5[w + 2 * BLOCK], a3 = s1[w + 3 * BLOCK], b3 = s5[w + 3 * BLOCK];
-      pair(w, a0, b0);
-      pair(w + BLOCK, a1, b1);
-      pair(w + 2 * BLOCK, a2, b2);
-      pair(w + 3 * BLOCK, a3, b3);
-      planes.add8(a0, b0, a1, b1, a2, b2, a3, b3);
-    }
-    for (; w < W; w += BLOCK) {
-      const uint32_t a = s1[w], b = s5[w];
-      pair(w, a, b);
-      planes.add1(a);
-      planes.add1(b);
-    }
-    const uint32_t bs = planes.index_sum();
-    // the sums over the warp in 32 bits (a warp's c1, c5 < 2^17, sw < 2^31,
-    // bs < 2^23: they fit), then the 64-bit count and checksum once per warp
-    uint32_t wc1 = c1, wc5 = c5, wsw = sw, wbs = bs, wbl = below32;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      wc1 += __shfl_down_sync(kFullMask, wc1, o);
-      wc5 += __shfl_down_sync(kFullMask, wc5, o);
-      wsw += __shfl_down_sync(kFullMask, wsw, o);
-      wbs += __shfl_down_sync(kFullMask, wbs, o);
-      wbl += __shfl_down_sync(kFullMask, wbl, o);
-    }
-    uint64_t cnt = (uint64_t)wc1 + wc5, below = wbl;
-    uint64_t sum = (uint64_t)wc1 * (6 * K0 + 1) + (uint64_t)wc5 * (6 * K0 + 5) + 6ull * wsw + 6ull * W * wbs;
-    if (FUSED && threadIdx.x == 0) sh_tile = t_begin + atomicAdd(counter, 1u);  // read after the next barrier
-    block_sum3_warps<BLOCK>(cnt, sum, below, red);
-    if (threadIdx.x == 0) {
-      if (K0 == 0) {  // 2 and 3 are outside the residue arrays (Section 2.1)
-        const uint64_t e2 = (p.lo <= 2 && 2 < p.hi), e3 = (p.lo <= 3 && 3 < p.hi);
-        cnt += e2 + e3;
-        below += e2 + e3;
-        sum += 2 * e2 + 3 * e3;
+      // popcount, checksum, and the count below the segment boundary (if any).
+      // Word w holds indices w + b W: their values sum to
+      // popc * (6 (K0 + w) + r) + 6 w popc + 6 W * (sum of the set bit positions b),
+      // so a thread accumulates, in 32 bits, the class counts c1 / c5, the
+      // word-weighted count sw and the bit-position sum bs of its words
+      // (sw < 2^15 * 64 * (W / BLOCK) < 2^32), and forms the 64-bit sum once.
+      uint32_t c1 = 0, c5 = 0, sw = 0, below32 = 0;
+      BitPlanes planes;  // the bit-position sum, four word pairs at a time
+      const int has_b = sh_has_boundary;
+      const int64_t t1 = has_b ? sh_t1 : 0, t5 = has_b ? sh_t5 : 0;
+      auto pair = [&](uint32_t w, uint32_t a, uint32_t b) {
+        if (LIST) p.bitmap[(uint64_t)t * W + w] = make_uint2(a, b);
+        const uint32_t ca = __popc(a), cb = __popc(b);
+        c1 += ca;
+        c5 += cb;
+        sw += w * (ca + cb);
+        if (has_b)
+          below32 += __popc(a & below_mask(t1, w, tg.logW, W)) + __popc(b & below_mask(t5, w, tg.logW, W));
+      };
+      uint32_t w = threadIdx.x;
+      for (; w + 3 * BLOCK < W; w += 4 * BLOCK) {
+        const uint32_t a0 = s1[w], b0 = s5[w], a1 = s1[w + BLOCK], b1 = s5[w + BLOCK];
+        const uint32_t a2 = s1[w + 2 * BLOCK], b2 = s5[w + 2 * BLOCK], a3 = s1[w + 3 * BLOCK], b3 = s5[w + 3 * BLOCK];
+        pair(w, a0, b0);
+        pair(w + BLOCK, a1, b1);
+        pair(w + 2 * BLOCK, a2, b2);
+        pair(w + 3 * BLOCK, a3, b3);
+        planes.add8(a0, b0, a1, b1, a2, b2, a3, b3);
       }
-      if (LIST) {
-        p.tile_counts[t] = (uint32_t)cnt;
+      for (; w < W; w += BLOCK) {
+        const uint32_t a = s1[w], b = s5[w];
+        pair(w, a, b);
+        planes.add1(a);
+        planes.add1(b);
       }
-      if (p.count) atomicAdd(p.count, (unsigned long long)cnt);
-      if (p.checksum) atomicAdd(p.checksum, (unsigned long long)sum);
-      if (p.seg_width && cnt) {
-        if (has_b) {
-          if (below) atomicAdd(p.bins + sh_bin0, (unsigned long long)below);
-          if (cnt - below) atomicAdd(p.bins + sh_bin0 + 1, (unsigned long long)(cnt - below));
-        } else {
-          atomicAdd(p.bins + sh_bin0, (unsigned long long)cnt);
+      const uint32_t bs = planes.index_sum();
+      // the sums over the warp in 32 bits (a warp's c1, c5 < 2^17, sw < 2^31,
+      // bs < 2^23: they fit), then the 64-bit count and checksum once per warp
+      uint32_t wc1 = c1, wc5 = c5, wsw = sw, wbs = bs, wbl = below32;
+  #pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        wc1 += __shfl_down_sync(kFullMask, wc1, o);
+        wc5 += __shfl_down_sync(kFullMask, wc5, o);
+        wsw += __shfl_down_sync(kFullMask, wsw, o);
+        wbs += __shfl_down_sync(kFullMask, wbs, o);
+        wbl += __shfl_down_sync(kFullMask, wbl, o);
+      }
+      uint64_t cnt = (uint64_t)wc1 + wc5, below = wbl;
+      uint64_t sum = (uint64_t)wc1 * (6 * K0 + 1) + (uint64_t)wc5 * (6 * K0 + 5) + 6ull * wsw + 6ull * W * wbs;
+      if (FUSED && threadIdx.x == 0) sh_tile = t_begin + atomicAdd(counter, 1u);  // read after the next barrier
+      block_sum3_warps<BLOCK>(cnt, sum, below, red);
+      if (threadIdx.x == 0) {
+        if (K0 == 0) {  // 2 and 3 are outside the residue arrays (Section 2.1)
+          const uint64_t e2 = (p.lo <= 2 && 2 < p.hi), e3 = (p.lo <= 3 && 3 < p.hi);
+          cnt += e2 + e3;
+          below += e2 + e3;
+          sum += 2 * e2 + 3 * e3;
         }
-      }
-    }
-    if (FUSED) {
-      // the tile's output offset, then its survivors straight from shared memory
-      if (warp == 0) {
-        const uint64_t c = __shfl_sync(kFullMask, cnt, 0);  // thread 0 holds the tile's count
-        uint64_t excl = 0;
-        const bool ok = lookback_prefix_warp(p.tile_state, t, c, &excl);
-        if (lane == 0) {
-          sh_lb_ok = ok;
-          if (!ok) atomicExch(p.error, 1ull);
-          sh_excl = excl;
+        if (LIST) {
+          p.tile_counts[t] = (uint32_t)cnt;
         }
-      }
-      __syncthreads();
-      if (sh_lb_ok) {
-        uint64_t off = sh_excl;
-        uint32_t *stage_w = smem + p.stage_off;
-        uint32_t *warp_cnt = stage_w + fused_stage_bytes(BLOCK) / sizeof(uint32_t);
-        if (K0 == 0 && threadIdx.x == 0) {  // 2 and 3 first
-          uint64_t o = off;
-          const bool e2 = p.lo <= 2 && 2 < p.hi, e3 = p.lo <= 3 && 3 < p.hi;
-          if (p.out_bytes == 4) {
-            if (e2 && o < p.cap) ((uint32_t *)p.out)[o] = 2;
-            o += e2;
-            if (e3 && o < p.cap) ((uint32_t *)p.out)[o] = 3;
+        if (p.count) atomicAdd(p.count, (unsigned long long)cnt);
+        if (p.checksum) atomicAdd(p.checksum, (unsigned long long)sum);
+        if (p.seg_width && cnt) {
+          if (has_b) {
+            if (below) atomicAdd(p.bins + sh_bin0, (unsigned long long)below);
+            if (cnt - below) atomicAdd(p.bins + sh_bin0 + 1, (unsigned long long)(cnt - below));
           } else {
-            if (e2 && o < p.cap) ((uint64_t *)p.out)[o] = 2;
-            o += e2;
-            if (e3 && o < p.cap) ((uint64_t *)p.out)[o] = 3;
+            atomicAdd(p.bins + sh_bin0, (unsigned long long)cnt);
           }
         }
-        if (K0 == 0) off += (p.lo <= 2 && 2 < p.hi) + (p.lo <= 3 && 3 < p.hi);
-        if (p.out_bytes == 4)
-          compact_tile_smem<BLOCK, uint32_t>(s1, s5, tg.logW, K0, off, (uint32_t *)p.out, p.cap, warp_cnt,
-                                             (uint8_t *)stage_w);
-        else
-          compact_tile_smem<BLOCK, uint64_t>(s1, s5, tg.logW, K0, off, (uint64_t *)p.out, p.cap, warp_cnt,
-                                             (uint8_t *)stage_w);
       }
-    }
+      if (FUSED) {
+        // the tile's output offset, then its survivors straight from shared memory
+        if (warp == 0) {
+          const uint64_t c = __shfl_sync(kFullMask, cnt, 0);  // thread 0 holds the tile's count
+          uint64_t excl = 0;
+          const bool ok = lookback_prefix_warp(p.tile_state, t, c, &excl);
+          if (lane == 0) {
+            sh_lb_ok = ok;
+            if (!ok) atomicExch(p.error, 1ull);
+            sh_excl = excl;
+          }
+        }
+        __syncthreads();
+        if (sh_lb_ok) {
+          uint64_t off = sh_excl;
+          uint32_t *stage_w = smem + p.stage_off;
+          uint32_t *warp_cnt = stage_w + fused_stage_bytes(BLOCK) / sizeof(uint32_t);
+          if (K0 == 0 && threadIdx.x == 0) {  // 2 and 3 first
+            uint64_t o = off;
+            const bool e2 = p.lo <= 2 && 2 < p.hi, e3 = p.lo <= 3 && 3 < p.hi;
+            if (p.out_bytes == 4) {
+              if (e2 && o < p.cap) ((uint32_t *)p.out)[o] = 2;
+              o += e2;
+              if (e3 && o < p.cap) ((uint32_t *)p.out)[o] = 3;
+            } else {
+              if (e2 && o < p.cap) ((uint64_t *)p.out)[o] = 2;
+              o += e2;
+              if (e3 && o < p.cap) ((uint64_t *)p.out)[o] = 3;
+            }
+          }
+          if (K0 == 0) off += (p.lo <= 2 && 2 < p.hi) + (p.lo <= 3 && 3 < p.hi);
+          if (p.out_bytes == 4)
+            compact_tile_smem<BLOCK, uint32_t>(s1, s5, tg.logW, K0, off, (uint32_t *)p.out, p.cap, warp_cnt,
+                                               (uint8_t *)stage_w);
+          else
+            compact_tile_smem<BLOCK, uint64_t>(s1, s5, tg.logW, K0, off, (uint64_t *)p.out, p.cap, warp_cnt,
+                                               (uint8_t *)stage_w);
+        }
+      }
+    }  // active
     // the next tile and its pattern offsets (a warp other than thread 0's)
     const uint32_t tn = FUSED ? sh_tile : t + gridDim.x;
     if (threadIdx.x >= 32 && threadIdx.x < 32 + (uint32_t)p.npat && tn < t_end)
@@ -467,12 +518,66 @@ namespace {
 template <int BLOCK, int MODE>
 void launch_mode(sieve_ctx *ctx, const RangeKernelParams &p, const BucketParams *b, int grid, size_t smem) {
   if (b) {
-    range_tiles_kernel<BLOCK, MODE, true><<<grid, BLOCK, smem, ctx->stream>>>(p, *b);
+    range_tiles_kernel<BLOCK, MODE, kLargeBuckets><<<grid, BLOCK, smem, ctx->stream>>>(p, *b);
   } else {
     BucketParams none;
     memset(&none, 0, sizeof(none));
-    range_tiles_kernel<BLOCK, MODE, false><<<grid, BLOCK, smem, ctx->stream>>>(p, none);
+    range_tiles_kernel<BLOCK, MODE, kLargeTiles><<<grid, BLOCK, smem, ctx->stream>>>(p, none);
   }
+}
+
+// The cluster-segment kernel for MODE (count or list bitmap) and BLOCK.
+template <int BLOCK>
+const void *cluster_kernel(int mode) {
+  return mode == kModeListBitmap ? (const void *)range_tiles_kernel<BLOCK, kModeListBitmap, kLargeCluster>
+                                 : (const void *)range_tiles_kernel<BLOCK, kModeCount, kLargeCluster>;
+}
+
+const void *dispatch_cluster_kernel(int threads, int mode) {
+  switch (threads) {
+    case 256: return cluster_kernel<256>(mode);
+    case 512: return cluster_kernel<512>(mode);
+    default: return cluster_kernel<1024>(mode);
+  }
+}
+
+// Launch configuration of a cluster-segment launch: `grid` CTAs (a multiple
+// of C) in one-dimensional clusters of C.
+struct ClusterLaunch {
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  ClusterLaunch(int threads, uint32_t C, int grid, size_t smem, cudaStream_t st) {
+    memset(&cfg, 0, sizeof(cfg));
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+};
+
+// Clusters of C CTAs that can be resident at once for this kernel (0: none).
+int cluster_capacity(int threads, int mode, uint32_t C, size_t smem, int *nclusters) {
+  ClusterLaunch cl(threads, C, (int)C, smem, nullptr);
+  *nclusters = 0;
+  SIEVE_CUDA_TRY(cudaOccupancyMaxActiveClusters(nclusters, dispatch_cluster_kernel(threads, mode), &cl.cfg));
+  return SIEVE_OK;
+}
+
+int launch_cluster(sieve_ctx *ctx, int threads, const RangeKernelParams &p, int mode, int grid, size_t smem) {
+  ClusterLaunch cl(threads, p.cluster, grid, smem, ctx->stream);
+  BucketParams none;
+  memset(&none, 0, sizeof(none));
+  const void *fn = dispatch_cluster_kernel(threads, mode);
+  void *args[] = {(void *)&p, (void *)&none};
+  SIEVE_CUDA_TRY(cudaLaunchKernelExC(&cl.cfg, fn, args));
+  ctx->launches++;
+  return SIEVE_OK;
 }
 
 template <int BLOCK>
@@ -497,19 +602,28 @@ int launch_range_tiles(sieve_ctx *ctx, const RangeKernelParams &p, const BucketP
 template <int BLOCK>
 int occupancy(int *blocks, bool list, size_t smem) {
   cudaError_t e = list ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                             blocks, range_tiles_kernel<BLOCK, kModeListBitmap, false>, BLOCK, smem)
+                             blocks, range_tiles_kernel<BLOCK, kModeListBitmap, kLargeTiles>, BLOCK, smem)
                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                             blocks, range_tiles_kernel<BLOCK, kModeCount, false>, BLOCK, smem);
+                             blocks, range_tiles_kernel<BLOCK, kModeCount, kLargeTiles>, BLOCK, smem);
   SIEVE_CUDA_TRY(e);
   return SIEVE_OK;
 }
 
 template <int BLOCK, int MODE>
 int set_smem_attr_mode(int bytes) {
-  SIEVE_CUDA_TRY(cudaFuncSetAttribute(range_tiles_kernel<BLOCK, MODE, false>,
+  SIEVE_CUDA_TRY(cudaFuncSetAttribute(range_tiles_kernel<BLOCK, MODE, kLargeTiles>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  SIEVE_CUDA_TRY(cudaFuncSetAttribute(range_tiles_kernel<BLOCK, MODE, true>,
+  SIEVE_CUDA_TRY(cudaFuncSetAttribute(range_tiles_kernel<BLOCK, MODE, kLargeBuckets>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  if constexpr (MODE != kModeListFused) {
+    SIEVE_CUDA_TRY(cudaFuncSetAttribute(range_tiles_kernel<BLOCK, MODE, kLargeCluster>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    // clusters of 16 CTAs are beyond the portable size of 8; a device that
+    // refuses them reports no capacity for them later
+    if (cudaFuncSetAttribute(range_tiles_kernel<BLOCK, MODE, kLargeCluster>,
+                             cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+      cudaGetLastError();
+  }
   return SIEVE_OK;
 }
 
@@ -860,9 +974,6 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
     SIEVE_CUDA_TRY(cudaMemsetAsync(acc, 0, 2 * sizeof(unsigned long long), st));
   }
 
-  BucketPlan plan;
-  const bool use_buckets = ntiles && plan_buckets(ctx, table, g, &plan);
-  const uint32_t nwaves = use_buckets ? (ntiles + plan.wave - 1) / plan.wave : 1;
   // single-pass list: device output, 512 or 1024 threads, and room in shared
   // memory for the emission staging (it reuses the warp-band starts' space)
   const int nwarps = threads / 32;
@@ -871,6 +982,13 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
                                fused_stage_bytes(threads) + (size_t)nwarps * 32 * sizeof(uint32_t));
   const bool fused = req.list && dev_out && threads != 256 && ctx->opt.list_single_pass &&
                      fused_smem <= (size_t)ctx->smem_optin;
+  // cluster segments (option cluster_ctas): not with the single-pass list,
+  // and only while every needed prime is below 2^31 (the inverse-of-6 start)
+  const uint32_t C = ctx->opt.cluster_ctas;
+  const bool use_cluster = C >= 2 && ntiles && !fused && np && table.host_primes[np - 1] < 0x80000000u;
+  BucketPlan plan;
+  const bool use_buckets = !use_cluster && ntiles && plan_buckets(ctx, table, g, &plan);
+  const uint32_t nwaves = use_buckets ? (ntiles + plan.wave - 1) / plan.wave : 1;
 
   // scratch layout: [bins (host-output case)] [tile counts] [offsets] [bitmap]
   // (two-pass list) or [tile states] [tile counters] [error word] (single pass)
@@ -929,7 +1047,24 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
     phase_event(ctx, 0);
   }
   if (ntiles) {
-    if (use_buckets) {
+    if (use_cluster) {
+      // one launch of clusters of C CTAs, each cluster taking segments of C
+      // consecutive tiles in grid-stride order
+      p.cluster = C;
+      p.i_cluster = std::max(host_prime_count_le_table(table, (uint64_t)ctx->opt.cluster_threshold * L), i_split);
+      int ncl = 0;
+      rc = cluster_capacity(threads, mode, C, smem, &ncl);
+      if (rc != SIEVE_OK) return rc;
+      if (ncl < 1) {
+        set_error("no cluster of %u CTAs of %d threads and %zu bytes of shared memory fits on the device", C,
+                  threads, smem);
+        return SIEVE_ERR_INVALID;
+      }
+      const uint64_t nseg = (ntiles + C - 1) / C;
+      rc = launch_cluster(ctx, threads, p, mode, (int)(std::min<uint64_t>(nseg, (uint64_t)ncl) * C), smem);
+      if (rc != SIEVE_OK) return rc;
+      if (ctx->phase_timing) ctx->ph.cluster_ctas = C;
+    } else if (use_buckets) {
       // the bucket sieve: per wave, the scatter, then the wave's tiles
       BucketParams &bk = plan.b;
       const uint32_t wave = plan.wave;
