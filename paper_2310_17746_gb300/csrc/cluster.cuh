@@ -81,16 +81,44 @@ __device__ __forceinline__ void cluster_strike(uint32_t *s1, uint32_t *s5, uint3
     else
       cluster_and(cluster_map(a + 4u * (kl & wmask), owner), m);
   };
-  for (uint64_t i = (uint64_t)i_lo + (uint64_t)rank * BLOCK + threadIdx.x; i < np_seg; i += (uint64_t)C * BLOCK) {
-    const uint32_t P = __ldg(primes + i);
+  auto one = [&](uint32_t P, uint64_t m, uint2 c) {
     const uint64_t Kc = ((uint64_t)P * P - 1) / 6;  // P^2 = 6 Kc + 1: nothing to strike below P^2
     const uint64_t K0 = Ks > Kc ? Ks : Kc;
-    if (K0 >= Ks + slen) continue;
+    if (K0 >= Ks + slen) return;
     uint32_t r1, r5;
-    starts_from_inverse(K0, P, __ldg(magic + i), __ldg(cinv + i), r1, r5);
+    starts_from_inverse(K0, P, m, c, r1, r5);
     const uint64_t base = K0 - Ks;
     for (uint64_t k = base + r1; k < slen; k += P) hit((uint32_t)k, s1, a1);
     for (uint64_t k = base + r5; k < slen; k += P) hit((uint32_t)k, s5, a5);
+  };
+  // one lane per prime; the next prime's table entries are loaded before the
+  // current one is struck, so that their latency overlaps the strikes (a
+  // segment streams the whole table above i_lo)
+  const uint64_t step = (uint64_t)C * BLOCK;
+  uint64_t i = (uint64_t)i_lo + (uint64_t)rank * BLOCK + threadIdx.x;
+  uint32_t P = 0;
+  uint64_t m = 0;
+  uint2 c = make_uint2(0, 0);
+  if (i < np_seg) {
+    P = __ldg(primes + i);
+    m = __ldg(magic + i);
+    c = __ldg(cinv + i);
+  }
+  while (i < np_seg) {
+    const uint64_t in = i + step;
+    uint32_t Pn = 0;
+    uint64_t mn = 0;
+    uint2 cn = make_uint2(0, 0);
+    if (in < np_seg) {
+      Pn = __ldg(primes + in);
+      mn = __ldg(magic + in);
+      cn = __ldg(cinv + in);
+    }
+    one(P, m, c);
+    P = Pn;
+    m = mn;
+    c = cn;
+    i = in;
   }
 }
 
