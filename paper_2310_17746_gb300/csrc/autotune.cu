@@ -352,10 +352,10 @@ extern "C" int sieve_tune_cache_store(sieve_ctx *ctx, const char *path, const ch
            "{\"device\": \"%s\", \"sms\": %d, \"workload\": \"%s\", \"tile_bits\": %u, \"block_threads\": %u, "
            "\"ctas_per_sm\": %u, \"group_hits\": %u, \"presieve_groups\": %u, \"batch_tile_bits\": %u, "
            "\"chunk_primes\": %u, \"bucket_threshold\": %u, \"bucket_wave\": %u, \"bucket_scatter\": %u, "
-           "\"ms\": %.6f}",
+           "\"list_single_pass\": %u, \"cluster_ctas\": %u, \"cluster_threshold\": %u, \"ms\": %.6f}",
            dev.c_str(), ctx->num_sms, workload, o.tile_bits, o.block_threads, o.ctas_per_sm, o.group_hits,
            o.presieve_groups, o.batch_tile_bits, o.chunk_primes, o.bucket_threshold, o.bucket_wave,
-           o.bucket_scatter, ms);
+           o.bucket_scatter, o.list_single_pass, o.cluster_ctas, o.cluster_threshold, ms);
   CacheEntry mine;
   mine.line = line;
   mine.device = dev;
@@ -418,6 +418,10 @@ extern "C" int sieve_tune_cache_load(sieve_ctx *ctx, const char *path, const cha
     if (entry_num(e.line, "bucket_wave", &bw) && bw >= 1 && bw <= 16) o.bucket_wave = (uint32_t)bw;
     double bs = 0;
     if (entry_num(e.line, "bucket_scatter", &bs) && bs >= 0 && bs <= 2) o.bucket_scatter = (uint32_t)bs;
+    double sp = 0, cc = 0, ct = 0;  // nor these, before the one-pass list and cluster segments
+    if (entry_num(e.line, "list_single_pass", &sp) && sp >= 0 && sp <= 1) o.list_single_pass = (uint32_t)sp;
+    if (entry_num(e.line, "cluster_ctas", &cc) && cc >= 0 && cc <= 16) o.cluster_ctas = (uint32_t)cc;
+    if (entry_num(e.line, "cluster_threshold", &ct) && ct >= 0 && ct <= 1024) o.cluster_threshold = (uint32_t)ct;
     rc = sieve_set_options(ctx, &o);  // validates every field
     if (rc != SIEVE_OK) return rc;
     double t = 0;

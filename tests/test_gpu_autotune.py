@@ -41,6 +41,8 @@ def test_autotune_range_result_equals_oracle(torch, tmp_path):
         path = str(tmp_path / "tune.json")
         sv.tune_cache_store(path, "count 1e10+2e9", ms)
         sv.tune_cache_store(path, "other workload", 1.0)
+        sv.set_options(cluster_ctas=8, cluster_threshold=16)
+        sv.tune_cache_store(path, "cluster segments", 2.0)
     with binding.Sieve(10**12) as sv2:
         assert sv2.options() == default
         assert sv2.tune_cache_load(path, "missing workload") is None
@@ -48,7 +50,11 @@ def test_autotune_range_result_equals_oracle(torch, tmp_path):
         opts, ms2 = sv2.tune_cache_load(path, "count 1e10+2e9")
         assert opts == best and abs(ms2 - ms) < 1e-3
         doc = json.load(open(path))
-        assert len(doc["entries"]) == 2
+        assert len(doc["entries"]) == 3
+        got = sv2.range_count(lo, hi)
+        assert (got.count, got.checksum) == oracle.count_range(lo, hi)
+        opts3, _ = sv2.tune_cache_load(path, "cluster segments")
+        assert opts3["cluster_ctas"] == 8 and opts3["cluster_threshold"] == 16
         got = sv2.range_count(lo, hi)
         assert (got.count, got.checksum) == oracle.count_range(lo, hi)
         # a corrupt entry is refused and leaves the options alone
