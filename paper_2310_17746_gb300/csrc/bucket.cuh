@@ -231,34 +231,60 @@ __global__ void __launch_bounds__(SB) bucket_scatter_direct_kernel(const BucketP
     else
       b.overflow[key] = 1;
   };
-  for (;;) {
-    const uint64_t i = (uint64_t)b.i_large + blockIdx.x + (uint64_t)b.ncta * atomicAdd(&next_m, 1u);
-    if (i >= b.i_end) break;
-    const uint32_t P = __ldg(b.primes + i);
+  // one prime at a time per thread; the next prime's index and table entries
+  // are fetched before the current prime is walked, so that their latency
+  // (the table streams from L2 or DRAM) overlaps its hits
+  auto take = [&]() -> uint64_t {
+    return (uint64_t)b.i_large + blockIdx.x + (uint64_t)b.ncta * atomicAdd(&next_m, 1u);
+  };
+  uint64_t i = take();
+  uint32_t P = 0;
+  uint64_t m = 0;
+  uint2 c = make_uint2(0, 0);
+  if (i < b.i_end) {
+    P = __ldg(b.primes + i);
+    m = __ldg(b.magic + i);
+    c = __ldg(b.cinv + i);
+  }
+  while (i < b.i_end) {
+    const uint64_t in = take();
+    uint32_t Pn = 0;
+    uint64_t mn = 0;
+    uint2 cn = make_uint2(0, 0);
+    if (in < b.i_end) {
+      Pn = __ldg(b.primes + in);
+      mn = __ldg(b.magic + in);
+      cn = __ldg(b.cinv + in);
+    }
     const uint64_t Kc = ((uint64_t)P * P - 1) / 6;  // P^2 = 6 Kc + 1: no hit below P^2
     const uint64_t K0 = Kw > Kc ? Kw : Kc;
-    if (K0 >= Kw + wl64) continue;
-    uint32_t a1, a5;
-    starts_from_inverse(K0, P, __ldg(b.magic + i), __ldg(b.cinv + i), a1, a5);
-    const uint32_t base = (uint32_t)(K0 - Kw);
-    // four hits per trip: their slot atomics are independent, so they are in
-    // flight together instead of one at a time (64-bit index: k + 3P may pass
-    // 2^32 before the test ends the loop)
-    auto walk = [&](uint64_t k, uint32_t cls) {
-      for (; k + 3ull * P < wlen; k += 4ull * P) {
-        emit((uint32_t)k, cls);
-        emit((uint32_t)(k + P), cls);
-        emit((uint32_t)(k + 2ull * P), cls);
-        emit((uint32_t)(k + 3ull * P), cls);
-      }
-      for (; k < wlen; k += P) emit((uint32_t)k, cls);
-    };
-    walk(base + a1, 0);
-    walk(base + a5, 1);
+    if (K0 < Kw + wl64) {
+      uint32_t a1, a5;
+      starts_from_inverse(K0, P, m, c, a1, a5);
+      const uint32_t base = (uint32_t)(K0 - Kw);
+      // four hits per trip: their slot atomics are independent, so they are
+      // in flight together instead of one at a time (64-bit index: k + 3P may
+      // pass 2^32 before the test ends the loop)
+      auto walk = [&](uint64_t k, uint32_t cls) {
+        for (; k + 3ull * P < wlen; k += 4ull * P) {
+          emit((uint32_t)k, cls);
+          emit((uint32_t)(k + P), cls);
+          emit((uint32_t)(k + 2ull * P), cls);
+          emit((uint32_t)(k + 3ull * P), cls);
+        }
+        for (; k < wlen; k += P) emit((uint32_t)k, cls);
+      };
+      walk(base + a1, 0);
+      walk(base + a5, 1);
+    }
+    P = Pn;
+    m = mn;
+    c = cn;
+    i = in;
   }
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < ntl; i += SB)
-    b.counts[(size_t)i * b.ncta + blockIdx.x] = sub[i] < b.cap ? sub[i] : b.cap;
+  for (uint32_t j = threadIdx.x; j < ntl; j += SB)
+    b.counts[(size_t)j * b.ncta + blockIdx.x] = sub[j] < b.cap ? sub[j] : b.cap;
 }
 
 constexpr int kDrainUnroll = 8;

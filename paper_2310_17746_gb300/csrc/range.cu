@@ -761,6 +761,7 @@ static int range_geometry(const sieve_ctx *ctx, const DeviceTable &table, uint64
 }
 
 constexpr int kScatterBlock = 512;  // threads of bucket_scatter_kernel
+constexpr uint32_t kBucketPresieveGroups = 4;  // presieve groups copied when the bucket sieve runs
 constexpr int kScatterHits = 16;    // hits per thread per round
 
 // Upper bound on the sum of 1/p over the primes p in (a, b], a >= 286: with
@@ -818,17 +819,26 @@ static bool plan_buckets(const sieve_ctx *ctx, const DeviceTable &table, const R
   constexpr double kBucketMaxHits = 0.25;
   const sieve_options &o = ctx->opt;
   if (!o.bucket_threshold || g.ntiles < 2 || g.np == 0) return false;
-  const uint64_t T = (uint64_t)o.bucket_threshold * g.L;
-  uint32_t i_large = host_prime_count_le_table(table, T);
-  if (i_large < g.i_split) i_large = g.i_split;
-  if (g.np < i_large + kBucketMinPrimes) return false;
   const uint32_t Pmax = table.host_primes[g.np - 1];
   if (Pmax >= 0x80000000u) return false;
-  const uint32_t Plo = table.host_primes[i_large];
-  const double S = prime_reciprocal_sum_bound(std::max<double>(Plo - 1, 286.0), (double)Pmax);
-  const double n_large = (double)(g.np - i_large);
-  const double e_tile = 2.0 * g.L * S;  // expected bucket entries per tile
-  if (e_tile / n_large > kBucketMaxHits) return false;
+  // bucket_threshold x L is the lowest threshold; while the primes above it
+  // hit a tile too often, raise it by a quarter (a range whose top primes sit
+  // just above 4 L keeps its buckets for the primes above 5 L: [5e13, +1e11)
+  // 43.8 ms without them, 40.8 with the primes above 6 L)
+  uint64_t T = (uint64_t)o.bucket_threshold * g.L;
+  uint32_t i_large = 0;
+  double e_tile = 0.0;
+  for (;;) {
+    i_large = host_prime_count_le_table(table, T);
+    if (i_large < g.i_split) i_large = g.i_split;
+    if (g.np < i_large + kBucketMinPrimes) return false;
+    const uint32_t Plo = table.host_primes[i_large];
+    const double S = prime_reciprocal_sum_bound(std::max<double>(Plo - 1, 286.0), (double)Pmax);
+    const double n_large = (double)(g.np - i_large);
+    e_tile = 2.0 * g.L * S;  // expected bucket entries per tile
+    if (e_tile / n_large <= kBucketMaxHits) break;
+    T += T / 4;
+  }
   if (!plan) return true;
   const bool sorted = o.bucket_scatter == 2 ||
                       (o.bucket_scatter == 0 && e_tile * g.grid * sizeof(uint32_t) > kBucketDirectMaxBytes);
@@ -989,6 +999,25 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
   BucketPlan plan;
   const bool use_buckets = !use_cluster && ntiles && plan_buckets(ctx, table, g, &plan);
   const uint32_t nwaves = use_buckets ? (ntiles + plan.wave - 1) / plan.wave : 1;
+  size_t fused_smem_used = fused_smem;
+  if (use_buckets && ctx->opt.presieve_groups > kBucketPresieveGroups) {
+    // with the bucket sieve at most kBucketPresieveGroups groups are copied:
+    // a wave's bucket entries (tens of MB) and the larger groups' patterns
+    // then compete for L2, and those patterns cost more than the strikes
+    // they save ([1e14, +1e11): 39.2 ms with 4 groups, 42.5 with 7, 45.6
+    // with 8; the headline, without buckets, is fastest with 7)
+    p.npat = 1 + kBucketPresieveGroups;
+    p.i_first = first_struck_prime_index(kBucketPresieveGroups);
+    const size_t starts_bytes = (size_t)(i_split - p.i_first) * sizeof(uint2);
+    smem = (size_t)L / 4 + starts_bytes;
+    fused_smem_used = (size_t)L / 4 + std::max(align_up(starts_bytes, 16), fused_stage_bytes(threads) +
+                                                                             (size_t)nwarps * 32 * sizeof(uint32_t));
+    if (std::max(smem, fused ? fused_smem_used : 0) > (size_t)ctx->smem_optin) {
+      set_error("tile of %u bits with %u warp-band primes needs %zu bytes of shared memory", L,
+                i_split - p.i_first, smem);
+      return SIEVE_ERR_INVALID;
+    }
+  }
 
   // scratch layout: [bins (host-output case)] [tile counts] [offsets] [bitmap]
   // (two-pass list) or [tile states] [tile counters] [error word] (single pass)
@@ -1032,7 +1061,7 @@ int run_range(sieve_ctx *ctx, const DeviceTable &table, const RangeRequest &req,
     p.cap = req.cap;
     p.out_bytes = (uint32_t)req.out_bytes;
     p.stage_off = 2 * (L / 32);
-    smem = fused_smem;
+    smem = fused_smem_used;
   } else if (req.list) {
     p.tile_counts = (uint32_t *)(scr + off_counts);
     p.bitmap = (uint2 *)(scr + off_bitmap);
