@@ -474,7 +474,7 @@ def batch_leg(steps: int, warmup: int) -> dict:
         "e2e": {"value": nq / statistics.mean(te), "unit": "queries/s",
                 "h2d_bytes_per_step": int(nq * 17), "d2h_bytes_per_step": int(nq * 16 + (nq + 1) * 8 + need * 8)},
         "list_write_gbs": need * 8 / t_dev / 1e9,
-        "autotuned": {k: tuned[k] for k in ("batch_tile_bits", "block_threads", "chunk_primes")},
+        "autotuned": {k: tuned[k] for k in ("batch_tile_bits", "block_threads", "chunk_primes", "presieve_groups")},
         "autotune_s": tune_s, "kernels_per_call": per_call_launches,
         "l2": "outputs (6 GB of primes) exceed L2; no flush",
     }
@@ -569,7 +569,7 @@ def serving_leg(rates=(1000, 3000, 10000, 30000, 100000), seconds: float = 1.0, 
     scratch = torch.empty(1 << 27, dtype=torch.int64, device=dev)  # 1 GiB landing zone for lists
     out = {"workload": "Poisson arrivals, seed 1: lo = floor(10^U(6,18)), width = floor(10^U(3,9)), "
                        "list with probability 0.2; base primes <= 1e9 on the device", "rates": [],
-           "autotuned": {"options": {k: tuned[k] for k in ("batch_tile_bits", "block_threads", "chunk_primes")},
+           "autotuned": {"options": {k: tuned[k] for k in ("batch_tile_bits", "block_threads", "chunk_primes", "presieve_groups")},
                          "sample": "512 requests of the serving distribution, seed 7", "sample_ms": tuned_ms,
                          "seconds": tune_s}}
     srv = binding.Server(sv, pool_bytes=32 << 30)

@@ -310,9 +310,10 @@ int sieve_range_each(sieve_ctx *ctx, const uint64_t *lo, const uint64_t *hi, con
  * context's options (returned in *best, time in *best_ms; either may be
  * NULL).  Every candidate's results must equal the first candidate's, else
  * the call fails with SIEVE_ERR_CUDA and the options are left unchanged.
- *   sieve_autotune_batch: batch_tile_bits x block_threads x chunk_primes on
- *     the given batch (host arrays, as sieve_range_batch); allocates and frees
- *     its own device outputs.
+ *   sieve_autotune_batch: batch_tile_bits {2^15 .. 2^19} x block_threads
+ *     {512, 1024} x chunk_primes {2^13, 2^15, 2^17} on the given batch (host
+ *     arrays, as sieve_range_batch), then presieve_groups {4 .. 7} with the
+ *     winner's other settings; allocates and frees its own device outputs.
  *   sieve_autotune_range: tile_bits {2^18, 2^19} x block_threads {512, 1024}
  *     x ctas_per_sm {0, 1, 2} (512 threads only) x group_hits {3, 4, 5, 6, 8}
  *     x presieve_groups {5, 6, 7, 8} on the count of [lo, hi) (a sample of the
