@@ -160,9 +160,22 @@ __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK > 0 ? 1024 / BLOCK : 1)) 
       const uint64_t span = qd.k_end - qd.k_begin;
       uint32_t *gq = a.slot_bm + qd.slot_base;
       const uint64_t stream = l2_policy_evict_first(), keep = l2_policy_evict_last();
-      for (uint32_t i = it.i0 + threadIdx.x; i < it.i1; i += BLOCK) {
-        const uint32_t P = ld_hint_u32(a.primes + i, stream);
-        const uint64_t m = ld_hint_u64(a.magic + i, stream);
+      // the next prime's entries are loaded before the current prime is
+      // walked, so that their latency overlaps its atomics
+      uint32_t i = it.i0 + threadIdx.x;
+      uint32_t Pn = 0;
+      uint64_t mn = 0;
+      if (i < it.i1) {
+        Pn = ld_hint_u32(a.primes + i, stream);
+        mn = ld_hint_u64(a.magic + i, stream);
+      }
+      for (; i < it.i1; i += BLOCK) {
+        const uint32_t P = Pn;
+        const uint64_t m = mn;
+        if (i + BLOCK < it.i1) {
+          Pn = ld_hint_u32(a.primes + i + BLOCK, stream);
+          mn = ld_hint_u64(a.magic + i + BLOCK, stream);
+        }
         uint64_t k1, k5;
         if ((uint64_t)P * P <= Bq && P < 0x80000000u) {  // the inverse-of-6 start (= Table 1's)
           uint32_t i1, i5;
