@@ -462,7 +462,8 @@ int sieve_measure_smem_atomics(int device, double *conflict_free, double *random
  * microseconds per call).  The paper has no counterpart: this backs the
  * roofline figures of the tile kernel and the list compaction. */
 typedef struct {
-  double sieve_ms;    /* the tile kernel: strikes, count, bitmap write-out in list mode */
+  double sieve_ms;    /* the tile kernel: strikes, count, bitmap write-out in list mode
+                         (sieve_range_batch: the batch's whole graph, upload to compaction) */
   double scan_ms;     /* list mode: the scan of per-tile counts (0 otherwise) */
   double compact_ms;  /* list mode: the compaction kernel (0 otherwise) */
   uint64_t tiles;     /* tiles the tile kernel sieved */
@@ -470,6 +471,8 @@ typedef struct {
   uint64_t listed;    /* list mode: primes the compaction wrote */
   uint64_t bucket_waves; /* waves of the bucket sieve (0: not used) */
   uint64_t cluster_ctas; /* CTAs per cluster of the cluster segments (0: not used) */
+  double batch_plan_ms;  /* sieve_range_batch: host time of planning the batch (work items,
+                            their cost order, the plan buffer) and preparing its buffers */
 } sieve_phase_times;
 
 /* enable != 0 turns phase timing on (creating the events), 0 turns it off.

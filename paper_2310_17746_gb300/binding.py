@@ -74,7 +74,8 @@ class ServerConfig(ctypes.Structure):
 class PhaseTimes(ctypes.Structure):
     _fields_ = [("sieve_ms", ctypes.c_double), ("scan_ms", ctypes.c_double), ("compact_ms", ctypes.c_double),
                 ("tiles", ctypes.c_uint64), ("tile_len", ctypes.c_uint64), ("listed", ctypes.c_uint64),
-                ("bucket_waves", ctypes.c_uint64), ("cluster_ctas", ctypes.c_uint64)]
+                ("bucket_waves", ctypes.c_uint64), ("cluster_ctas", ctypes.c_uint64),
+                ("batch_plan_ms", ctypes.c_double)]
 
 
 class ServerStats(ctypes.Structure):

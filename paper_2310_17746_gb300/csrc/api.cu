@@ -30,22 +30,39 @@ int cuda_fail(cudaError_t e, const char *what) {
 // ---------------------------------------------------------------- helpers
 
 uint64_t isqrt_u64(uint64_t n) {
-  if (n < 2) return n;
-  uint64_t x = (uint64_t)1 << ((64 - __builtin_clzll(n) + 1) / 2);
-  for (;;) {  // Newton from above
-    uint64_t y = (x + n / x) >> 1;
-    if (y >= x) break;
-    x = y;
-  }
-  while (x > n / x) x--;
-  while (x + 1 <= n / (x + 1)) x++;
+  // the double square root is within a few units of the integer root (its
+  // rounding matters only near 2^53 and above); exact 128-bit products settle it
+  uint64_t x = (uint64_t)std::sqrt((double)n);
+  if (x > 0xFFFFFFFFull) x = 0xFFFFFFFFull;
+  while (x > 0 && (unsigned __int128)x * x > n) x--;
+  while ((unsigned __int128)(x + 1) * (x + 1) <= n) x++;
   return x;
 }
 
 uint32_t host_prime_count_le_table(const DeviceTable &t, uint64_t s) {
   const uint32_t *b = t.host_primes, *e = t.host_primes + t.nprimes;
   if (s >= 0xFFFFFFFFull) return t.nprimes;
-  return (uint32_t)(std::upper_bound(b, e, (uint32_t)s) - b);
+  const uint64_t j = s >> kCountIndexShift;
+  if (t.count_idx && j + 1 < t.count_idx_n) {  // only the bucket holding s: the primes below it are <= s,
+    e = t.host_primes + t.count_idx[j + 1];    // the primes above it > s
+    b = t.host_primes + t.count_idx[j];
+  }
+  return (uint32_t)(std::upper_bound(b, e, (uint32_t)s) - t.host_primes);
+}
+
+// Build the context table's prime-count index over values up to its limit.
+static void build_count_index(sieve_ctx *c) {
+  const uint64_t n = (c->table.limit >> kCountIndexShift) + 2;
+  c->h_count_idx.assign(n, 0);
+  const size_t np = c->h_primes.size();
+  size_t i = 0;
+  for (uint64_t j = 0; j < n; j++) {
+    const uint64_t v = j << kCountIndexShift;
+    while (i < np && c->h_primes[i] < v) i++;
+    c->h_count_idx[j] = (uint32_t)i;
+  }
+  c->table.count_idx = c->h_count_idx.data();
+  c->table.count_idx_n = n;
 }
 
 int ensure_scratch(sieve_ctx *ctx, size_t bytes) {
@@ -361,6 +378,7 @@ static int build_base_table(sieve_ctx *c, uint64_t limit) {
   c->table.host_primes = c->h_primes.data();
   c->table.nprimes = (uint32_t)total;
   c->table.limit = limit;
+  build_count_index(c);
   return SIEVE_OK;
 }
 
@@ -430,6 +448,7 @@ int extend_base_table(sieve_ctx *c, uint64_t new_limit) {
   } while (0);
   if (rc != SIEVE_OK) {
     c->h_primes.resize(n0);
+    c->table.host_primes = c->h_primes.data();  // the resize above may have moved the host copy
     cudaFree(np_);
     cudaFree(nm);
     cudaFree(nc);
@@ -447,6 +466,7 @@ int extend_base_table(sieve_ctx *c, uint64_t new_limit) {
   c->table.host_primes = c->h_primes.data();
   c->table.nprimes = (uint32_t)(n0 + n);
   c->table.limit = new_limit;
+  build_count_index(c);
   c->max_hi = new_limit >= 0xB504F333ull ? (1ull << 63) : (new_limit + 1) * (new_limit + 1);
   c->table_epoch++;
   return SIEVE_OK;

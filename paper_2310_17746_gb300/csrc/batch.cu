@@ -2,6 +2,7 @@
 // and the public sieve_range_batch call.  The data layout and the two kinds of
 // work items are described in batch.cuh.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstddef>
 #include <cstring>
@@ -571,10 +572,26 @@ constexpr uint64_t kBatchGraphKernels = 5;
 
 namespace {
 
+// ln x for x >= 1, to about 1e-5 absolute, for the cost model: x = 2^e m with
+// m in [1, 2), and ln m = 2 atanh(t), t = (m - 1) / (m + 1) <= 1/3, summed to
+// the t^7 term.  (The planner evaluates it tens of times per work item, in
+// the binary searches that size the items; the library log was a large part
+// of planning a batch.)
+double fast_ln(double x) {
+  uint64_t b;
+  memcpy(&b, &x, sizeof(b));
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;
+  b = (b & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull;
+  double m;
+  memcpy(&m, &b, sizeof(m));
+  const double t = (m - 1.0) / (m + 1.0), t2 = t * t;
+  return e * 0.6931471805599453 + 2.0 * t * (1.0 + t2 * (1.0 / 3.0 + t2 * (1.0 / 5.0 + t2 * (1.0 / 7.0))));
+}
+
 // ln ln x for the strike-count estimate: the class-1 and class-5 multiples of
 // the primes in (a, b] among n indices number about 2 n (ln ln b - ln ln a)
 // (Mertens' second theorem).
-double lnln(double x) { return std::log(std::log(std::max(x, 23.0))); }
+double lnln(double x) { return fast_ln(fast_ln(std::max(x, 23.0))); }
 
 // Relative cost units of the work an item does (one unit ~ one strike in
 // shared memory).  An atomic AND in global memory is priced at many strikes:
@@ -1026,9 +1043,18 @@ extern "C" int sieve_range_batch(sieve_ctx *ctx, const uint64_t *lo, const uint6
   if (rc != SIEVE_OK) return rc;
   uint64_t *target = dev ? values : (uint64_t *)ctx->d_stage;
   uint64_t tcap = dev ? cap : ctx->stage_bytes / sizeof(uint64_t);
+  const auto t_plan = std::chrono::steady_clock::now();
   if ((rc = batch_plan(r, lo, hi, mode, nq, target, tcap, 0, nullptr, nullptr)) != SIEVE_OK) return rc;
   if ((rc = batch_prepare(r)) != SIEVE_OK) return rc;
+  if (ctx->phase_timing) {
+    ctx->ph = sieve_phase_times{};
+    ctx->ph.batch_plan_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_plan).count();
+    ctx->ph_recorded = 0;
+    if (cudaEventRecord(ctx->ph_ev[0], st) == cudaSuccess) ctx->ph_recorded |= 1u;
+  }
   if ((rc = batch_launch(r)) != SIEVE_OK) return rc;
+  if (ctx->phase_timing && cudaEventRecord(ctx->ph_ev[1], st) == cudaSuccess) ctx->ph_recorded |= 2u;
   const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   SIEVE_CUDA_TRY(cudaMemcpyAsync(cnt, r.d_acc, nq * sizeof(sieve_count_result), kind, st));
   SIEVE_CUDA_TRY(cudaMemcpyAsync(offsets, r.d_offsets, (nq + 1) * sizeof(uint64_t), kind, st));

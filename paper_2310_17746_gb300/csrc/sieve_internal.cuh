@@ -261,7 +261,16 @@ struct DeviceTable {
   const uint32_t *host_primes = nullptr;  // host copy of primes
   uint32_t nprimes = 0;
   uint64_t limit = 0;
+  // host: count_idx[j] = number of table primes below j << kCountIndexShift,
+  // for j < count_idx_n (optional: without it counts search the whole table)
+  const uint32_t *count_idx = nullptr;
+  uint64_t count_idx_n = 0;
 };
+
+// Bucket width of the host prime-count index: a count searches one bucket of
+// about 2^12 / ln x primes instead of the whole table (a batch plan makes
+// three counts per query).
+constexpr uint32_t kCountIndexShift = 12;
 
 struct BatchRunner;  // batch.cu
 
@@ -281,6 +290,7 @@ struct sieve_ctx {
   uint64_t *d_magic = nullptr;
   uint2 *d_cinv = nullptr;
   std::vector<uint32_t> h_primes;  // host copy of the base table
+  std::vector<uint32_t> h_count_idx;  // its prime-count index (DeviceTable::count_idx)
   // presieve patterns in the sliced layout, one set per tile width W = 2^logW
   struct SlicedSet {
     uint32_t *d = nullptr;
