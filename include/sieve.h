@@ -454,13 +454,13 @@ int sieve_measure_smem_atomics(int device, double *conflict_free, double *random
 
 /* ------------------------------------------------------------- phase timing */
 
-/* Device time of the phases of the last single-range call on this context
- * that reached the tile kernel (sieve_count, sieve_primes, sieve_primes_u32,
- * sieve_range, sieve_segment_counts), measured with CUDA events on the
- * context's stream
- * while phase timing is enabled (it is off by default; the events cost a few
- * microseconds per call).  The paper has no counterpart: this backs the
- * roofline figures of the tile kernel and the list compaction. */
+/* Device time of the phases of the last call on this context that reached
+ * the tile kernel (sieve_count, sieve_primes, sieve_primes_u32, sieve_range,
+ * sieve_segment_counts) or a batch graph (sieve_range_batch), measured with
+ * CUDA events on the context's stream while phase timing is enabled (it is
+ * off by default; the events cost a few microseconds per call), and a batch
+ * call's host planning time.  The paper has no counterpart: this backs the
+ * roofline figures of the tile kernel, the list compaction and the batch. */
 typedef struct {
   double sieve_ms;    /* the tile kernel: strikes, count, bitmap write-out in list mode
                          (sieve_range_batch: the batch's whole graph, upload to compaction) */

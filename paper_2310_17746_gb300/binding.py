@@ -294,12 +294,14 @@ class Sieve:
         _check(self._lib.sieve_set_options(self._h, ctypes.byref(o)), "sieve_set_options")
 
     def set_phase_timing(self, enable: bool = True) -> None:
-        """Turn per-phase CUDA-event timing of single-range calls on or off."""
+        """Turn per-phase timing of single-range and batch calls on or off."""
         _check(self._lib.sieve_set_phase_timing(self._h, 1 if enable else 0), "sieve_set_phase_timing")
 
     def phase_times(self) -> dict:
         """Device times (ms) of the last single-range call's tile kernel, scan
-        and compaction, with its tile count, tile length and listed primes."""
+        and compaction, with its tile count, tile length and listed primes;
+        after a batch call, its graph's device time (sieve_ms) and its host
+        planning time (batch_plan_ms)."""
         t = PhaseTimes()
         _check(self._lib.sieve_get_phase_times(self._h, ctypes.byref(t)), "sieve_get_phase_times")
         return {k: getattr(t, k) for k, _ in PhaseTimes._fields_}

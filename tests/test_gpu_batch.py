@@ -235,3 +235,21 @@ def test_batch_strip_primes_squared_inside_queries(sv):
         _check_against_oracle(lo, hi, mode, cnt, off, vals)
     finally:
         _restore(sv, opts)
+
+
+def test_batch_phase_times(sv):
+    """With phase timing on, a batch call reports its host planning time and
+    its graph's device time; the results are unchanged."""
+    q = workloads.random_small_ranges(300, seed=11, max_lo=10**12, max_width=2_000_000)
+    cnt0, off0, vals0 = sv.range_batch(q.lo, q.hi, q.mode)
+    sv.set_phase_timing(True)
+    try:
+        cnt, off, vals = sv.range_batch(q.lo, q.hi, q.mode)
+        ph = sv.phase_times()
+    finally:
+        sv.set_phase_timing(False)
+    assert ph["batch_plan_ms"] > 0 and ph["sieve_ms"] > 0
+    np.testing.assert_array_equal(cnt, cnt0)
+    np.testing.assert_array_equal(off, off0)
+    np.testing.assert_array_equal(vals, vals0)
+    _check_against_oracle(q.lo, q.hi, q.mode, cnt, off, vals)
