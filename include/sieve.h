@@ -98,8 +98,10 @@ typedef struct {
   uint32_t bucket_threshold; /* single ranges: base primes above bucket_threshold x tile_bits go
                               through the bucket sieve (located once per wave of tiles, their hits
                               sorted into per-tile buckets that each tile drains) when they are
-                              many and each hits a tile rarely; 0 = off (every prime is located
-                              in every tile); at most 64                                     */
+                              many and each hits a tile rarely; where the primes above it hit
+                              too often, the planner raises the threshold in steps of a quarter
+                              (it is the lowest one); with buckets the presieve copies at most 4
+                              groups; 0 = off (every prime is located in every tile); at most 64 */
   uint32_t bucket_wave;    /* bucket sieve: tiles per CTA in one wave (1..16)                  */
   uint32_t bucket_scatter; /* bucket sieve: 1 = direct scatter (each hit stored at once), 2 =
                               sorted scatter (a round's hits sorted by tile in shared memory,
