@@ -222,8 +222,8 @@ __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK > 0 ? 1024 / BLOCK : 1)) 
     const uint32_t split = qd.i_split < it.i1 ? qd.i_split : it.i1;
     warp_band_starts<BLOCK>(starts, B, tg.len, a.primes, a.magic, a.cinv, it.i0, split);
     __syncthreads();
-    strike_primes<BLOCK>(s1, s5, B, tg, a.primes, a.magic, a.cinv, starts, it.i0, split, sh_np, sh_allsq != 0,
-                         &sh_next, B / 6);  // B / 6 here rather than K0: measured faster in this kernel
+    strike_primes<BLOCK, true>(s1, s5, B, tg, a.primes, a.magic, a.cinv, starts, it.i0, split, sh_np,
+                               sh_allsq != 0, &sh_next, B / 6);  // B / 6 rather than K0: measured faster here
     __syncthreads();
     if (merged) {
       // AND the shared-memory result into the query's bitmap in global memory

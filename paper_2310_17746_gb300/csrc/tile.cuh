@@ -166,14 +166,14 @@ __device__ __forceinline__ void warp_band_starts(uint2 *starts, uint64_t B, uint
 // prime is skipped).  (Loading the
 // constants only for primes below the tile span, so that larger ones keep a
 // one-remainder miss test, was slower: the load then waits for the prime.)
-template <int BLOCK>
+template <int BLOCK, bool PREFETCH = false>
 __device__ __forceinline__ void strike_lane_band(uint32_t *s1, uint32_t *s5, uint64_t B, const TileGeom &tg,
                                                  const uint32_t *__restrict__ primes,
                                                  const uint64_t *__restrict__ magic,
                                                  const uint2 *__restrict__ cinv, uint32_t i_lo, uint32_t np,
                                                  bool all_sq, uint64_t K0);
 
-template <int BLOCK>
+template <int BLOCK, bool PREFETCH = false>
 __device__ __forceinline__ void strike_primes(uint32_t *s1, uint32_t *s5, uint64_t B, const TileGeom &tg,
                                               const uint32_t *__restrict__ primes,
                                               const uint64_t *__restrict__ magic, const uint2 *__restrict__ cinv,
@@ -196,17 +196,47 @@ __device__ __forceinline__ void strike_primes(uint32_t *s1, uint32_t *s5, uint64
   }
   // primes from the warp band's end up to np (or lane_end: above it the
   // bucket sieve applies them) by one lane each
-  strike_lane_band<BLOCK>(s1, s5, B, tg, primes, magic, cinv, split > i_first ? split : i_first,
-                          np < lane_end ? np : lane_end, all_sq, K0);
+  strike_lane_band<BLOCK, PREFETCH>(s1, s5, B, tg, primes, magic, cinv, split > i_first ? split : i_first,
+                                    np < lane_end ? np : lane_end, all_sq, K0);
 }
+
+// L2 prefetch (TMA bulk prefetch, a hint: no data moves to the SM) of the
+// table entries [a, b) of the primes, their reciprocals and their inverse-of-6
+// constants; the spans are cut to 16-byte boundaries inside each array.
+__device__ __forceinline__ void prefetch_table_l2(const uint32_t *primes, const uint64_t *magic, const uint2 *cinv,
+                                                  uint32_t a, uint32_t b) {
+  if (b <= a) return;
+  auto pf = [](const void *base, uint32_t elem, uint32_t a, uint32_t b) {
+    const uintptr_t s = ((uintptr_t)base + (uintptr_t)a * elem + 15) & ~(uintptr_t)15;
+    const uintptr_t e = ((uintptr_t)base + (uintptr_t)b * elem) & ~(uintptr_t)15;
+    if (e > s) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s), "r"((uint32_t)(e - s)) : "memory");
+  };
+  pf(primes, 4, a, b);
+  pf(magic, 8, a, b);
+  pf(cinv, 8, a, b);
+}
+
+// Blocks of BLOCK primes by which thread 0 keeps the table ahead of the
+// one-lane band: far up a lane's prime costs a few dozen instructions, far
+// less than a table line's trip from DRAM.  Only entries from index
+// kLanePrefetchFirst on (primes above about 3.5e7, 40 MB of table below them)
+// are prefetched: those stream from DRAM, while the table below stays in L2,
+// where the prefetches only cost (the 4096-query batch, whose primes stop
+// below it: 12.4 -> 13.6 ms with them; serving requests up to 1e18: 24.2 ->
+// 22.4 ms per 512).  Only the batch kernel, which serves the far requests,
+// is compiled with them: in the range kernel the untaken test alone cost 2 %
+// at the headline.
+constexpr uint32_t kLanePrefetchBlocks = 4;
+constexpr uint32_t kLanePrefetchFirst = 1u << 21;
 
 // Strike the primes with table index in [i_lo, np) into the tile whose index
 // 0 is value B (K0 = B / 6), one lane per prime: each lane locates its prime's
 // first hits from the inverse-of-6 constants (the Table 1 start, see
 // starts_from_inverse) or, where the P^2 clamp can apply, with Table 1 itself
 // (all_sq: the caller knows that every prime below np has P^2 <= B and
-// P < 2^31, so the test per prime is skipped).
-template <int BLOCK>
+// P < 2^31, so the test per prime is skipped).  PREFETCH: thread 0 keeps the
+// far part of the table (see kLanePrefetchFirst) in L2 ahead of the lanes.
+template <int BLOCK, bool PREFETCH>
 __device__ __forceinline__ void strike_lane_band(uint32_t *s1, uint32_t *s5, uint64_t B, const TileGeom &tg,
                                                  const uint32_t *__restrict__ primes,
                                                  const uint64_t *__restrict__ magic,
@@ -222,12 +252,21 @@ __device__ __forceinline__ void strike_lane_band(uint32_t *s1, uint32_t *s5, uin
     uint32_t P = 0;
     uint64_t m = 0;
     uint2 c = make_uint2(0, 0);
+    constexpr uint32_t kAhead = kLanePrefetchBlocks * BLOCK;
+    const bool far = PREFETCH && np > kLanePrefetchFirst;  // the stream reaches the table kept in DRAM
+    auto ahead = [&](uint32_t a, uint32_t b) {  // [a, b) within [kLanePrefetchFirst, np)
+      prefetch_table_l2(primes, magic, cinv, a > kLanePrefetchFirst ? a : kLanePrefetchFirst, b < np ? b : np);
+    };
+    if (far && threadIdx.x == 0) ahead(i_lo, i_lo + kAhead);
     if (i < np) {
       P = __ldg(primes + i);
       m = __ldg(magic + i);
       c = __ldg(cinv + i);
     }
     while (i < np) {
+      // thread 0 (at i = i_lo + 2 k BLOCK) requests the two blocks that come
+      // into the prefetch window as the CTA moves on by two blocks
+      if (far && threadIdx.x == 0) ahead(i + kAhead, i + kAhead + 2 * BLOCK);
       const uint32_t in = i + BLOCK;
       uint32_t Pb = 0;
       uint64_t mb = 0;
