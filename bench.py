@@ -62,11 +62,49 @@ def dist_env():
     return rank, world, local
 
 
+# Device time of the count per 1e11 numbers at height x, in ms: linear in
+# the number of base primes below sqrt(x) (each is located in every tile),
+# measured on one GB300 for windows of 1e11 starting at 1e11 ... 2e13 (15.4,
+# 17.3, 18.6, 20.4, 23.0, 25.7, 27.9, 33.3 ms; the fit is within 1 %)
+COST_A_MS, COST_B_MS = 13.58, 6.27e-5
+_PI_SQRT = None
+
+
+def range_cost_ms(lo: int, hi: int, steps: int = 2048) -> float:
+    """Modelled count time of [lo, hi) (midpoint rule over the cost density)."""
+    global _PI_SQRT
+    import numpy as np
+    if _PI_SQRT is None:
+        flags = np.zeros(10**7 + 1, dtype=np.int64)
+        flags[small_primes(10**7)] = 1
+        _PI_SQRT = np.cumsum(flags)
+    x = lo + (np.arange(steps) + 0.5) * ((hi - lo) / steps)
+    r = np.minimum(np.sqrt(x).astype(np.int64), len(_PI_SQRT) - 1)
+    return float(np.sum(COST_A_MS + COST_B_MS * _PI_SQRT[r]) * (hi - lo) / steps / 1e11)
+
+
+_RANK_RANGES: list[tuple[int, int]] = []
+
+
 def rank_range(rank: int) -> tuple[int, int]:
-    """Rank r sieves a range of width 1e12: rank 0 [2, 1e12], rank r ((r)e12, (r+1)e12]."""
-    if rank == 0:
-        return 2, WIDTH + 1
-    return rank * WIDTH + 1, (rank + 1) * WIDTH + 1
+    """Rank 0 sieves [2, 1e12] (the headline configuration); rank r > 0 the
+    next contiguous range whose modelled count time equals rank 0's, so that
+    the work per GPU stays fixed as ranks are added (weak scaling) and the
+    ranks finish together.  Widths are multiples of 6e6."""
+    if not _RANK_RANGES:
+        _RANK_RANGES.append((2, WIDTH + 1))
+    while len(_RANK_RANGES) <= rank:
+        target = range_cost_ms(*_RANK_RANGES[0])
+        lo = _RANK_RANGES[-1][1]
+        a, b = 1, WIDTH // 6_000_000  # width in units of 6e6: the cost grows with it
+        while a < b:
+            m = (a + b + 1) // 2
+            if range_cost_ms(lo, lo + m * 6_000_000) <= target:
+                a = m
+            else:
+                b = m - 1
+        _RANK_RANGES.append((lo, lo + a * 6_000_000))
+    return _RANK_RANGES[rank]
 
 
 # ---------------------------------------------------------------- accounting
@@ -788,7 +826,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": "count [2, 1e12] with 2^30-number block histogram (932 bins); "
-                               "rank r>0 sieves (r*1e12, (r+1)*1e12]",
+                               "rank r>0 sieves the next contiguous range of rank 0's modelled cost",
                    "lo": lo, "hi_exclusive": hi, "seg_width": SEG_WIDTH,
                    "tile_bits": opts["tile_bits"], "block_threads": opts["block_threads"],
                    "group_hits": opts["group_hits"],
