@@ -62,25 +62,10 @@ def dist_env():
     return rank, world, local
 
 
-# Device time of the count per 1e11 numbers at height x, in ms: linear in
-# the number of base primes below sqrt(x) (each is located in every tile),
-# measured on one GB300 for windows of 1e11 starting at 1e11 ... 2e13 (15.4,
-# 17.3, 18.6, 20.4, 23.0, 25.7, 27.9, 33.3 ms; the fit is within 1 %)
-COST_A_MS, COST_B_MS = 13.58, 6.27e-5
-_PI_SQRT = None
-
-
-def range_cost_ms(lo: int, hi: int, steps: int = 2048) -> float:
-    """Modelled count time of [lo, hi) (midpoint rule over the cost density)."""
-    global _PI_SQRT
-    import numpy as np
-    if _PI_SQRT is None:
-        flags = np.zeros(10**7 + 1, dtype=np.int64)
-        flags[small_primes(10**7)] = 1
-        _PI_SQRT = np.cumsum(flags)
-    x = lo + (np.arange(steps) + 0.5) * ((hi - lo) / steps)
-    r = np.minimum(np.sqrt(x).astype(np.int64), len(_PI_SQRT) - 1)
-    return float(np.sum(COST_A_MS + COST_B_MS * _PI_SQRT[r]) * (hi - lo) / steps / 1e11)
+def range_cost_ms(lo: int, hi: int) -> float:
+    """Modelled count time of [lo, hi) (the library's sharding cost model)."""
+    from paper_2310_17746_gb300 import shard
+    return shard.cost_ms(lo, hi)
 
 
 _RANK_RANGES: list[tuple[int, int]] = []

@@ -64,3 +64,14 @@ def test_sharded_equals_unsharded(world):
         assert (c, s) == (want_c, want_s), rank
         np.testing.assert_array_equal(np.frombuffer(bins, dtype=np.uint64), want_bins)
         np.testing.assert_array_equal(np.frombuffer(lst, dtype=np.uint64), want_list)
+
+
+def test_shard_bounds_balance_modelled_cost():
+    lo, hi = 2, 8 * 10**12
+    b = shard.shard_bounds(lo, hi, 8)
+    costs = [shard.cost_ms(x, y) for x, y in zip(b, b[1:])]
+    assert max(costs) - min(costs) <= 0.002 * max(costs)
+    widths = [y - x for x, y in zip(b, b[1:])]
+    assert all(w1 > w2 for w1, w2 in zip(widths, widths[1:]))  # higher shards are narrower
+    even = shard.shard_bounds(lo, hi, 8, balance=False)
+    assert max(y - x for x, y in zip(even, even[1:])) - min(y - x for x, y in zip(even, even[1:])) <= 12
