@@ -119,6 +119,8 @@ def _batch(args) -> int:
     sv = binding.Sieve(int(q.hi.max()) + 1)
     opts = {k: v for k, v in (("batch_tile_bits", args.batch_tile_bits), ("block_threads", args.block_threads),
                               ("chunk_primes", args.chunk_primes), ("group_hits", args.group_hits)) if v}
+    if args.presieve_groups >= 0:
+        opts["presieve_groups"] = args.presieve_groups
     if opts:
         sv.set_options(**opts)
     cnt = torch.zeros((nq, 2), dtype=torch.int64, device="cuda")
