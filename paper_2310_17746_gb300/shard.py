@@ -34,7 +34,7 @@ def _pi(y: np.ndarray) -> np.ndarray:
         for i in range(2, int(_PI_EXACT**0.5) + 1):
             if f[i]:
                 f[i * i::i] = False
-        _pi_table = np.cumsum(f, dtype=np.int64)
+        _pi_table = np.cumsum(f, dtype=np.int32)  # pi(1e7) = 664579
     y = np.asarray(y, dtype=np.float64)
     small = y <= _PI_EXACT
     out = np.empty_like(y)
